@@ -1,0 +1,137 @@
+"""Named synthetic workloads: tet-cube systems shaped like the paper's FEM scenes.
+
+Recipe (unit cube, side 1 m, h = 1/(n-1)):
+  * n^3 vertices, 5 tets per cell; rest positions jittered N(0, 0.05 h);
+  * deformed positions x = (I + G) X + N(0, 0.02 h), G_ij ~ U(-0.1, 0.1),
+    so the PSD projection of the stable Neo-Hookean Hessian is active;
+  * SNH Hessian with Young's modulus E, Poisson ratio nu, plus lumped
+    mass m_v / dt^2 on the diagonal (the system K + M / dt^2);
+  * contact stand-ins: PSD blocks k n n^T on vertex pairs, k log-uniform;
+  * right-hand sides N(0, 1), seed 2000 + rhs index.
+
+The stable Neo-Hookean F-space Hessian is linear in E at fixed nu (both
+Lame parameters scale with E and alpha = 1 + mu/lam does not), and PSD
+projection commutes with positive scaling, so systems that differ only in
+E share one set of element blocks computed at E = 1.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .hessians import (
+    contact_blocks,
+    lumped_mass_blocks,
+    near_pairs,
+    random_pairs,
+    snh_element_blocks,
+)
+from .mesh import adjacency_csr, tet_cube, tet_edges
+
+
+@dataclass
+class TetSystem:
+    n_grid: int
+    X: np.ndarray  # rest positions (V, 3)
+    rows: np.ndarray  # int32 (K,)  upper-triangle triplets, duplicates allowed
+    cols: np.ndarray  # int32 (K,)
+    blocks: np.ndarray  # float64 (K, 3, 3) row-major
+    adj_ptr: np.ndarray  # int32 (V+1,) mesh vertex graph (contacts excluded)
+    adj: np.ndarray  # int32
+    contacts: np.ndarray  # int32 (P, 2) contact vertex pairs
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_vertices(self):
+        return self.X.shape[0]
+
+
+@dataclass
+class _Geometry:
+    n: int
+    X: np.ndarray
+    tets: np.ndarray
+    unit_rows: np.ndarray
+    unit_cols: np.ndarray
+    unit_blocks: np.ndarray  # element blocks at E = 1
+    mass: tuple
+    contacts: np.ndarray
+    contact_trip: tuple
+    adj_ptr: np.ndarray
+    adj: np.ndarray
+    shuffle_seed: int
+
+
+def _geometry(n, nu, rho, dt, n_contacts, contact_mode, k_range, seed):
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n - 1)
+    X, tets = tet_cube(n, rng, jitter=0.05)
+    G = rng.uniform(-0.1, 0.1, (3, 3))
+    x = X @ (np.eye(3) + G).T + rng.normal(0.0, 0.02 * h, X.shape)
+    r_e, c_e, b_e = snh_element_blocks(X, x, tets, 1.0, nu)
+    mass = lumped_mass_blocks(X, tets, rho, dt)
+    V = X.shape[0]
+    if n_contacts > 0:
+        if contact_mode == "random":
+            pairs = random_pairs(rng, V, n_contacts)
+        else:
+            pairs = near_pairs(rng, X, n, n_contacts, 2.0 * h)
+        ctrip = contact_blocks(rng, pairs, *k_range)
+    else:
+        pairs = np.zeros((0, 2), np.int32)
+        ctrip = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros((0, 3, 3)))
+    ptr, adj = adjacency_csr(V, tet_edges(tets))
+    return _Geometry(n, X, tets, r_e, c_e, b_e, mass, pairs, ctrip, ptr, adj, seed + 7919)
+
+
+def _system(g, E, params):
+    rows = np.concatenate([g.unit_rows, g.mass[0], g.contact_trip[0]]).astype(np.int32)
+    cols = np.concatenate([g.unit_cols, g.mass[1], g.contact_trip[1]]).astype(np.int32)
+    blocks = np.concatenate([E * g.unit_blocks, g.mass[2], g.contact_trip[2]])
+    # shuffle so duplicates are not adjacent (as emitted by a parallel element loop)
+    perm = np.random.default_rng(g.shuffle_seed).permutation(rows.size)
+    return TetSystem(
+        n_grid=g.n,
+        X=g.X,
+        rows=rows[perm],
+        cols=cols[perm],
+        blocks=np.ascontiguousarray(blocks[perm]),
+        adj_ptr=g.adj_ptr,
+        adj=g.adj,
+        contacts=g.contacts,
+        params=dict(params, E=E),
+    )
+
+
+def make_tet_systems(n, Es, nu=0.4, rho=1000.0, dt=0.01, n_contacts=0,
+                     contact_mode="random", k_range=(1e2, 1e6), seed=1000):
+    """Systems on one n^3 tet cube that differ only in Young's modulus (list, one per E).
+
+    contact_mode "random" draws distinct uniform vertex pairs; "near" draws
+    pairs closer than 2h at rest (which may repeat mesh edges).
+    """
+    g = _geometry(n, nu, rho, dt, n_contacts, contact_mode, k_range, seed)
+    params = dict(n=n, nu=nu, rho=rho, dt=dt, n_contacts=n_contacts,
+                  contact_mode=contact_mode, seed=seed)
+    return [_system(g, E, params) for E in Es]
+
+
+def make_tet_system(n, E=1e5, **kw):
+    return make_tet_systems(n, [E], **kw)[0]
+
+
+def rhs(n_dof, nrhs, seed0=2000):
+    """nrhs right-hand sides N(0,1), each from seed seed0 + index; shape (nrhs, n_dof)."""
+    return np.stack([np.random.default_rng(seed0 + k).normal(size=n_dof) for k in range(nrhs)])
+
+
+def plain_small(seed=1001):
+    """16^3 cube (4,096 verts), E=1e5, 2,000 random contact pairs (2-level MAS, N=32)."""
+    return make_tet_system(16, E=1e5, n_contacts=2000, contact_mode="random", seed=seed)
+
+
+def stiffness_sweep(Es=(1e5, 1e7, 1e9), n=64, seed=1002):
+    """n^3 cube (64^3 = 262,144 verts), one system per E, 200k contact pairs within 2h
+    (scaled with the vertex count for other n); 3-level MAS, N=32."""
+    return make_tet_systems(n, Es, n_contacts=max(1, 200_000 * n ** 3 // 64 ** 3),
+                            contact_mode="near", seed=seed)

@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against closed forms, worked examples, brute force and
+dense linear algebra -- never against a retyping of the oracle's own formula."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import assembly, mas, partition, pcg
+from synth.workloads import make_tet_system, rhs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny_system(n=4, E=1e6, contacts=3, seed=7):
+    return make_tet_system(n, E=E, n_contacts=contacts, contact_mode="random", seed=seed)
+
+
+# ---------------------------------------------------------------- assembly (Sec. 5.2)
+
+
+def test_hash_key_layout():
+    # Sec. 5.2: first index in the high 32 bits, second in the low 32.
+    assert int(assembly.hash_key(1, 2)) == (1 << 32) + 2
+    assert int(assembly.hash_key(7, 0)) == 7 << 32
+
+
+def test_assembly_matches_dict_bruteforce():
+    rng = np.random.default_rng(0)
+    n, K = 9, 400
+    rows = rng.integers(0, n, K)
+    cols = rng.integers(0, n, K)
+    blocks = rng.normal(size=(K, 3, 3))
+    r1, c1, a1 = assembly.assemble(rows, cols, blocks)
+    r2, c2, a2 = assembly.assemble_dict(rows, cols, blocks)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
+    np.testing.assert_allclose(a1, a2, rtol=1e-13, atol=1e-13)
+    assert np.all(r1 <= c1)
+    k = assembly.hash_key(r1, c1)
+    assert np.all(np.diff(k) > 0)  # sorted, unique
+
+
+def test_assembly_recovers_split_matrix():
+    # Split every block of a known upper pattern into random summands
+    # (duplicates), add lower-triangle noise that must be ignored, shuffle:
+    # the reduction must give back the original blocks.
+    rng = np.random.default_rng(1)
+    n = 12
+    pat = sorted({(min(a, b), max(a, b)) for a, b in rng.integers(0, n, (60, 2))} | {(i, i) for i in range(n)})
+    truth = {p: rng.normal(size=(3, 3)) for p in pat}
+    rows, cols, blocks = [], [], []
+    for (r, c), B in truth.items():
+        k = int(rng.integers(1, 6))
+        parts = rng.normal(size=(k, 3, 3))
+        parts[-1] = B - parts[:-1].sum(0)
+        for P in parts:
+            rows.append(r), cols.append(c), blocks.append(P)
+        if r != c:  # a lower-triangle copy that is ignored
+            rows.append(c), cols.append(r), blocks.append(rng.normal(size=(3, 3)))
+    perm = rng.permutation(len(rows))
+    rid, cid, au = assembly.assemble(np.array(rows)[perm], np.array(cols)[perm], np.array(blocks)[perm])
+    assert [(int(a), int(b)) for a, b in zip(rid, cid)] == pat
+    for (r, c), B in zip(zip(rid.tolist(), cid.tolist()), au):
+        np.testing.assert_allclose(B, truth[(r, c)], atol=1e-12)
+
+
+def test_head_segmented_reduce_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "head_segmented_reduce.json")))
+    out = assembly.head_segmented_reduce(g["values"], g["tags"], width=g["width"])
+    assert out == g["output"]
+    # A warp boundary always opens a segment (Alg. FastSegmentReduction: LaneId == 0).
+    out2 = assembly.head_segmented_reduce([1] * 10, [1] + [0] * 9, width=4)
+    assert out2 == [4, None, None, None, 4, None, None, None, 2, None]
+
+
+def test_abd_two_level_equals_dense_jacobian_product():
+    # Sec. 5.1: the reduced Hessian is J^T A J with J = [I, x1 I, x2 I, x3 I]
+    # for body nodes and I for FEM nodes; compare with dense matrices.
+    rng = np.random.default_rng(2)
+    n_full, n_fem, n_bodies = 10, 4, 2
+    body = np.array([-1] * n_fem + [0, 0, 0, 1, 1, 1])
+    xbar = rng.normal(size=(n_full, 3))
+    K = 80
+    rows = rng.integers(0, n_full, K)
+    cols = rng.integers(0, n_full, K)
+    lo = np.minimum(rows, cols)
+    hi = np.maximum(rows, cols)
+    blocks = rng.normal(size=(K, 3, 3))
+    blocks[lo == hi] = blocks[lo == hi] + np.swapaxes(blocks[lo == hi], 1, 2)
+    rid, cid, au = assembly.assemble_abd(lo, hi, blocks, body, xbar, n_fem)
+    n_red = n_fem + 4 * n_bodies
+    got = assembly.to_dense(n_red, rid, cid, au)
+    # dense route
+    r0, c0, a0 = assembly.assemble_dict(lo, hi, blocks)
+    A = assembly.to_dense(n_full, r0, c0, a0)
+    J = np.zeros((3 * n_full, 3 * n_red))
+    for i in range(n_full):
+        if body[i] < 0:
+            J[3 * i : 3 * i + 3, 3 * i : 3 * i + 3] = np.eye(3)
+        else:
+            w = [1.0, *xbar[i]]
+            for a in range(4):
+                R = n_fem + 4 * body[i] + a
+                J[3 * i : 3 * i + 3, 3 * R : 3 * R + 3] = w[a] * np.eye(3)
+    np.testing.assert_allclose(got, J.T @ A @ J, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- SpMV (Sec. 5.3)
+
+
+def test_symmetric_spmv_equals_dense_product():
+    s = _tiny_system()
+    rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
+    V = s.n_vertices
+    A = assembly.to_dense(V, rid, cid, au)
+    x = np.random.default_rng(3).normal(size=(2, V, 3))
+    y = pcg.spmv(rid, cid, au, x)
+    for k in range(2):
+        np.testing.assert_allclose(y[k].ravel(), A @ x[k].ravel(), rtol=1e-12, atol=1e-9)
+    assert np.allclose(A, A.T)
+
+
+# ---------------------------------------------------------------- partition (Sec. 3.2)
+
+
+def test_partition_hand_worked_grid():
+    # 4x4 grid, N = 4.  Extents tie -> x; left = 4*ceil(4/2) = 8 vertices
+    # with x in {0, 1}; each half then splits along y: four 2x2 boxes,
+    # numbered left to right.
+    i, j = np.meshgrid(np.arange(4), np.arange(4), indexing="xy")
+    X = np.stack([i.ravel(), j.ravel(), np.zeros(16)], -1).astype(float)  # index = x + 4 y
+    part = partition.recursive_bisection(X, 4)
+    expect = np.array([0, 0, 2, 2, 0, 0, 2, 2, 1, 1, 3, 3, 1, 1, 3, 3])
+    assert np.array_equal(part, expect)
+    mp, rm = partition.map_remap(part, 4)
+    assert list(rm[:4]) == [0, 1, 4, 5] and list(rm[4:8]) == [8, 9, 12, 13]
+    assert np.all(rm[mp] == np.arange(16))
+
+
+@pytest.mark.parametrize("V,N", [(1, 32), (31, 32), (32, 32), (33, 32), (1000, 16), (4096, 32)])
+def test_partition_invariants(V, N):
+    X = np.random.default_rng(V).normal(size=(V, 3))
+    part = partition.recursive_bisection(X, N)
+    sizes = np.bincount(part)
+    M = -(-V // N)
+    assert part.max() + 1 == M  # Eq. num_subdomains with N_o = 0
+    assert np.all(sizes[:-1] == N) and 1 <= sizes[-1] <= N
+    mp, rm = partition.map_remap(part, N)
+    assert rm.size == N * M
+    assert np.array_equal(np.sort(mp), np.sort(np.nonzero(rm >= 0)[0]))
+    assert np.all(rm[mp] == np.arange(V))
+    assert np.all(mp // N == part)
+
+
+def test_partition_boxes_are_connected_on_tet_cube():
+    s = make_tet_system(16, n_contacts=0, seed=3)
+    part = partition.recursive_bisection(s.X, 32)
+    V = s.n_vertices
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    A = csr_matrix((np.ones(s.adj.size), s.adj, s.adj_ptr), shape=(V, V))
+    ncomp = [connected_components(A[p][:, p])[0] for p in (np.nonzero(part == q)[0] for q in range(part.max() + 1))]
+    assert max(ncomp) == 1
+
+
+# ---------------------------------------------------------------- MAS levels (supp. Alg. 2-5)
+
+
+def test_initial_hash_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "initial_hash_mask.json")))
+    N = g["domain_size"]
+    nodes = [g["node"]] + g["neighbours"]
+    slots = [g["node_slot"]] + g["neighbour_slots"]
+    item_of_u = np.full(max(nodes) + 1, 0, dtype=np.int64)
+    for u, s_ in zip(nodes, slots):
+        item_of_u[u] = s_
+    # nodes not listed get distinct far slots (outside domain 0)
+    unused = [u for u in range(item_of_u.size) if u not in nodes]
+    item_of_u[unused] = 1000 + np.arange(len(unused))
+    edges = np.array([[g["node"], v] for v in g["neighbours"]])
+    masks = mas.in_domain_masks(item_of_u, N, 2000, edges)
+    assert int(masks[g["node_slot"]]) == g["mask"]
+
+
+def _graph_from_edges(V, edges):
+    from synth.mesh import adjacency_csr
+
+    return adjacency_csr(V, np.array(edges))
+
+
+def test_case_study_morton_ordering_gives_three_levels():
+    # Sec. 3.1 case study, domain size 4, nodes a..p = 0..15 in Morton order.
+    # Level 0: only {b,d} connected in Omega_0; {f,h}, {i,j,k,l}, {m,o},
+    # {n,p} merge; b+d is placed before c (lowest order of merged nodes).
+    a, b, c, d, e, f, g, h, i, j, k, l, m, n, o, p = range(16)
+    edges = [(b, d), (f, h), (i, j), (j, k), (k, l), (m, o), (n, p), (g, i), (c, n), (e, m)]
+    ptr, adj = _graph_from_edges(16, edges)
+    lv = mas.build_levels(np.arange(16), 4, 8, ptr, adj)
+    assert lv.n_items[1] == 9  # a, bd, c | e, fh, g | ijkl | mo, np
+    assert list(lv.coarse[1][[a, b, d, c]]) == [0, 1, 1, 2]
+    assert lv.n_levels == 3  # the inefficient three-level hierarchy of the text
+
+
+def test_case_study_connectivity_grouping_gives_two_levels():
+    # Sec. 3.1: grouping by connectivity makes every level-0 domain one
+    # supernode; level 1 then holds 4 supernodes in 1 domain and stops.
+    edges = []
+    for q in range(4):
+        grp = [4 * q + t for t in range(4)]
+        edges += [(u, v) for u in grp for v in grp if u < v]
+    edges += [(3, 4), (7, 8), (11, 12), (0, 15)]
+    ptr, adj = _graph_from_edges(16, edges)
+    lv = mas.build_levels(np.arange(16), 4, 8, ptr, adj)
+    assert lv.n_levels == 2 and lv.n_items == [16, 4]
+    assert list(lv.coarse[1]) == [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4
+
+
+def test_contact_pairs_join_supernodes():
+    # Alg. 3: a contact pair inside a domain connects its two nodes.
+    ptr, adj = _graph_from_edges(8, [(0, 1), (2, 3)])
+    lv = mas.build_levels(np.arange(8), 4, 2, ptr, adj)
+    assert lv.n_items[1] == 6  # {0,1},{2,3} | 4,5,6,7
+    lv2 = mas.build_levels(np.arange(8), 4, 2, ptr, adj, contacts=np.array([[1, 2], [5, 6]]))
+    assert lv2.n_items[1] == 4  # {0,1,2,3} | 4,{5,6},7
+    assert list(lv2.coarse[1]) == [0, 0, 0, 0, 1, 2, 2, 3]
+
+
+def _component_invariants(lv, edges):
+    N = lv.N
+    for l in range(lv.n_levels - 1):
+        item = lv.coarse[l]
+        nxt_of_fine = lv.coarse[l + 1]
+        a = item[edges[:, 0]]
+        b = item[edges[:, 1]]
+        same_dom = a // N == b // N
+        # maximality: adjacent items in one domain share a supernode
+        assert np.all(nxt_of_fine[edges[same_dom, 0]] == nxt_of_fine[edges[same_dom, 1]])
+        # supernodes never span two domains; ids are domain-major
+        dom_of_super = {}
+        for u in range(item.size):
+            s_ = int(nxt_of_fine[u])
+            dom_of_super.setdefault(s_, set()).add(int(item[u]) // N)
+        assert all(len(v) == 1 for v in dom_of_super.values())
+        doms = [next(iter(dom_of_super[s_])) for s_ in sorted(dom_of_super)]
+        assert doms == sorted(doms)
+        assert lv.n_items[l + 1] <= int(lv.real[l].sum())
+
+
+def test_level_invariants_on_tet_cube():
+    s = _tiny_system(n=10, contacts=40, seed=11)
+    part = partition.recursive_bisection(s.X, 8)
+    mp, _ = partition.map_remap(part, 8)
+    lv = mas.build_levels(mp, 8, 5, s.adj_ptr, s.adj, s.contacts)
+    assert lv.n_levels >= 3
+    _component_invariants(lv, mas.fine_edges(s.adj_ptr, s.adj, s.contacts))
+
+
+# ---------------------------------------------------------------- MAS matrices / apply (Alg. 1, Eq. 4-6)
+
+
+def _system_and_partition(n=5, N=8, E=1e6, contacts=6, seed=5):
+    s = _tiny_system(n=n, E=E, contacts=contacts, seed=seed)
+    rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
+    part = partition.recursive_bisection(s.X, N)
+    mp, rm = partition.map_remap(part, N)
+    A = assembly.to_dense(s.n_vertices, rid, cid, au)
+    return s, rid, cid, au, mp, rm, A
+
+
+def test_single_domain_preconditioner_is_exact_inverse():
+    s, rid, cid, au, mp, rm, A = _system_and_partition(n=4, N=64)
+    M = mas.build_mas(mp, 64, 4, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    assert M.levels.n_levels == 1
+    r = np.random.default_rng(0).normal(size=3 * s.n_vertices)
+    np.testing.assert_allclose(M(r), np.linalg.solve(A, r), rtol=1e-9, atol=1e-12)
+    b = rhs(3 * s.n_vertices, 1)
+    mv = lambda v: pcg.spmv(rid, cid, au, v.reshape(-1, 3)).ravel()
+    _, it, rel = pcg.pcg(mv, lambda v: M(v), b, tol=1e-8)
+    assert it[0] == 1 and rel[0] <= 1e-8
+
+
+def test_one_level_is_block_jacobi():
+    # supplement Eq. 4: non-overlapping domains -> block-diagonal preconditioner.
+    s, rid, cid, au, mp, rm, A = _system_and_partition()
+    N = 8
+    M = mas.build_mas(mp, N, 1, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    r = np.random.default_rng(1).normal(size=3 * s.n_vertices)
+    z = np.zeros_like(r)
+    part = mp // N
+    for q in range(part.max() + 1):
+        nodes = np.nonzero(part == q)[0]
+        idx = (3 * nodes[:, None] + np.arange(3)).ravel()
+        z[idx] = np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+    np.testing.assert_allclose(M(r), z, rtol=1e-10, atol=1e-14)
+
+
+def test_domain_size_one_is_3x3_block_jacobi():
+    s, rid, cid, au, mp, rm, A = _system_and_partition()
+    part1 = partition.recursive_bisection(s.X, 1)
+    mp1, _ = partition.map_remap(part1, 1)
+    M = mas.build_mas(mp1, 1, 1, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    r = np.random.default_rng(2).normal(size=(s.n_vertices, 3))
+    z = np.stack([np.linalg.solve(A[3 * v : 3 * v + 3, 3 * v : 3 * v + 3], r[v]) for v in range(s.n_vertices)])
+    np.testing.assert_allclose(M(r), z, rtol=1e-10, atol=1e-14)
+
+
+def test_two_node_supernode_block_by_hand():
+    # Level-1 block of a supernode {0, 1} is A00 + A01 + A10 + A11 (Alg. 1).
+    rng = np.random.default_rng(3)
+    B = [rng.normal(size=(3, 3)) for _ in range(4)]
+    A00 = B[0] @ B[0].T + 5 * np.eye(3)
+    A11 = B[1] @ B[1].T + 5 * np.eye(3)
+    A22 = B[2] @ B[2].T + 5 * np.eye(3)
+    A01 = 0.3 * B[3]
+    rid = np.array([0, 0, 1, 2])
+    cid = np.array([0, 1, 1, 2])
+    au = np.stack([A00, A01, A11, A22])
+    ptr, adj = _graph_from_edges(3, [(0, 1)])
+    lv = mas.build_levels(np.array([0, 1, 2]), 2, 2, ptr, adj)
+    assert lv.n_items == [4, 2] and list(lv.coarse[1]) == [0, 0, 1]
+    mats = mas.level_matrices(lv, rid, cid, au)
+    np.testing.assert_allclose(mats[1][0][:3, :3], A00 + A01 + A01.T + A11, atol=1e-14)
+    np.testing.assert_allclose(mats[1][0][3:, 3:], A22, atol=1e-14)
+    np.testing.assert_allclose(mats[1][0][:3, 3:], 0.0)
+
+
+def test_level_matrices_equal_galerkin_products():
+    # Alg. 1's scatter equals S_d C_l A C_l^T S_d^T computed with dense 0/1 matrices.
+    s, rid, cid, au, mp, rm, A = _system_and_partition()
+    N = 8
+    lv = mas.build_levels(mp, N, 4, s.adj_ptr, s.adj, s.contacts)
+    assert lv.n_levels >= 2
+    mats = mas.level_matrices(lv, rid, cid, au)
+    V = s.n_vertices
+    for l in range(lv.n_levels):
+        n = lv.n_domains(l) * N
+        C = np.zeros((3 * n, 3 * V))
+        for u in range(V):
+            a = int(lv.coarse[l][u])
+            C[3 * a : 3 * a + 3, 3 * u : 3 * u + 3] = np.eye(3)
+        G = C @ A @ C.T
+        for d in range(lv.n_domains(l)):
+            sl = slice(3 * N * d, 3 * N * (d + 1))
+            np.testing.assert_allclose(mats[l][d], G[sl, sl], rtol=1e-12, atol=1e-9)
+
+
+def test_apply_equals_explicit_coarsener_sum_and_is_spd():
+    s, rid, cid, au, mp, rm, A = _system_and_partition()
+    M = mas.build_mas(mp, 8, 4, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    D = mas.dense_preconditioner(M.levels, M.invs)
+    rng = np.random.default_rng(4)
+    r1, r2 = rng.normal(size=(2, 3 * s.n_vertices))
+    np.testing.assert_allclose(M(r1), D @ r1, rtol=1e-10, atol=1e-14)
+    assert abs(r1 @ M(r2) - r2 @ M(r1)) <= 1e-12 * np.linalg.norm(r1) * np.linalg.norm(M(r2))
+    w = np.linalg.eigvalsh(0.5 * (D + D.T))
+    assert w.min() > 0
+    # MAS adds coarse corrections to block-Jacobi: r.M r >= r.M0 r
+    M0 = mas.build_mas(mp, 8, 1, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    assert r1 @ M(r1) >= r1 @ M0(r1)
+
+
+def test_not_spd_domain_is_reported():
+    rid = np.array([0, 0, 1])
+    cid = np.array([0, 1, 1])
+    au = np.stack([np.eye(3), 2 * np.eye(3), np.eye(3)])  # [[I, 2I], [2I, I]] indefinite
+    ptr, adj = _graph_from_edges(2, [(0, 1)])
+    with pytest.raises(mas.NotSPDError):
+        mas.build_mas(np.array([0, 1]), 2, 1, ptr, adj, None, rid, cid, au)
+
+
+# ---------------------------------------------------------------- PCG (Sec. 3.2)
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_pcg_matches_dense_solve(levels):
+    s, rid, cid, au, mp, rm, A = _system_and_partition(n=5, N=8, E=1e7)
+    M = mas.build_mas(mp, 8, levels, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    b = rhs(3 * s.n_vertices, 2)
+    mv = lambda v: pcg.spmv(rid, cid, au, v.reshape(-1, 3)).ravel()
+    x, it, rel = pcg.pcg(mv, lambda v: M(v), b, tol=1e-12)
+    for k in range(2):
+        xs = np.linalg.solve(A, b[k])
+        assert np.linalg.norm(x[k] - xs) <= 1e-9 * np.linalg.norm(xs)
+        assert np.linalg.norm(b[k] - A @ x[k]) <= 1e-11 * np.linalg.norm(b[k])
+        assert rel[k] <= 1e-12 and 1 <= it[k] <= 3 * s.n_vertices
+
+
+def test_pcg_fixed_iterations_and_zero_rhs():
+    s, rid, cid, au, mp, rm, A = _system_and_partition(n=4, N=8)
+    M = mas.build_mas(mp, 8, 2, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
+    mv = lambda v: pcg.spmv(rid, cid, au, v.reshape(-1, 3)).ravel()
+    b = np.zeros((2, 3 * s.n_vertices))
+    b[1] = rhs(3 * s.n_vertices, 1)[0]
+    x, it, rel = pcg.pcg(mv, lambda v: M(v), b, fixed_iters=3)
+    assert it[0] == 0 and np.all(x[0] == 0)
+    assert it[1] == 3
+    # after 3 steps the residual is smaller than at the start
+    assert np.linalg.norm(b[1] - A @ x[1]) < np.linalg.norm(b[1])
