@@ -1,0 +1,193 @@
+/*
+ * gipc_mas_pcg.h -- C ABI of the GB300 Newton-step linear solver.
+ *
+ * The library solves the Newton system P d = -grad E of implicit IPC
+ * (Sec. 3.2, Eq. tailor): it assembles the block-sparse Hessian from
+ * duplicate 3x3 blocks (Sec. 5.2), builds the connectivity-enhanced
+ * multilevel additive Schwarz (MAS) preconditioner (Sec. 3, supplement
+ * Sec. 2) and runs PCG (Sec. 3.2) -- all on one GPU.
+ *
+ * Conventions shared by every call
+ *   - Return value: GS_OK (0) or a negative GS_ERR_* status.  On error no
+ *     output handle is created and outputs may be partially written.
+ *   - "device" pointers are CUDA device pointers on the context's device;
+ *     "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library owns gs_mat / gs_mas handles until the
+ *     matching *_destroy call.
+ *   - All work is issued on the context's stream.  Calls that return sizes
+ *     or statuses synchronise that stream before returning.
+ *   - Indices are int32; block values are float64, each 3x3 block stored
+ *     row-major (9 consecutive doubles).
+ *   - Vectors hold 3 doubles per block row (x, y, z).  Several right-hand
+ *     sides are stored one after another: entry c of block row i of RHS k
+ *     is v[k * 3 * n + 3 * i + c].
+ */
+#ifndef GIPC_MAS_PCG_H
+#define GIPC_MAS_PCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define GS_OK 0
+#define GS_ERR_INVALID -1     /* bad argument: null pointer, size or index out of range */
+#define GS_ERR_CUDA -2        /* a CUDA runtime call failed (message: gs_last_error) */
+#define GS_ERR_NOT_SPD -3     /* non-positive pivot in a domain Cholesky, or p.Ap <= 0 */
+#define GS_ERR_MAXITER -4     /* PCG stopped at max_iter before reaching tol; x is written */
+#define GS_ERR_NONFINITE -5   /* NaN or Inf met in a reduction */
+#define GS_ERR_UNSUPPORTED -6 /* option outside the supported set (e.g. domain size > 32) */
+
+typedef struct gs_ctx_s* gs_ctx;
+typedef struct gs_mat_s* gs_mat;
+typedef struct gs_mas_s* gs_mas;
+
+/* Human-readable name of a status code (static string). */
+const char* gs_status_string(int status);
+/* Last error message recorded on this thread (static buffer, never null). */
+const char* gs_last_error(void);
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device`, issuing work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is
+ * borrowed, not owned.  Work buffers are allocated lazily from the
+ * device's stream-ordered memory pool and reused across calls. */
+int gs_create(gs_ctx* out, int device, void* stream);
+int gs_set_stream(gs_ctx ctx, void* stream);
+int gs_destroy(gs_ctx ctx);
+
+/* ---------------------------------------------------------------- assembly */
+/* Global Hessian assembly by hash-key reduction (Sec. 5.2, Alg.
+ * FastHashReduction and Alg. FastSegmentReduction).
+ *
+ * rows, cols: device int32[n_blocks], block row / column of every input
+ *   block, each in [0, n_block_rows).
+ * blocks: device double[n_blocks * 9], row-major 3x3 blocks.
+ * The inputs describe the full symmetric matrix: an input with
+ * row <= col is accumulated, an input with row > col is not consumed (its
+ * transpose is the block at (col, row)).  Duplicates are summed.
+ * Result (*out): the distinct keys in ascending (row, col) order with
+ * their summed blocks -- the paper's Sorted Symmetric Block Coordinates
+ * (Sec. 5.3) -- plus a block-row pointer.
+ * Errors: GS_ERR_INVALID for n_block_rows <= 0, n_blocks < 0, a null
+ * pointer with n_blocks > 0, or any index outside [0, n_block_rows). */
+int gs_assemble(gs_ctx ctx, int32_t n_block_rows, const int32_t* rows, const int32_t* cols,
+                const double* blocks, int64_t n_blocks, gs_mat* out);
+
+/* Two-level assembly of coupled FEM / affine-body (ABD) blocks (Sec. 5.1,
+ * Sec. 5.2 "unifying four block types").
+ * Inputs are 3x3 blocks in full-space node numbering (n_nodes nodes),
+ * with the same row <= col convention as gs_assemble.
+ * body_of_node: device int32[n_nodes], -1 for a FEM vertex, else the affine
+ *   body index in [0, n_bodies).  FEM vertices must be nodes 0..n_fem-1.
+ * xbar: device double[n_nodes * 3], rest coordinates of body nodes (read
+ *   for nodes with body_of_node >= 0).
+ * Level 1 reduces blocks per node pair; level 2 maps each reduced pair
+ * through the Jacobians J = [I, xbar_1 I, xbar_2 I, xbar_3 I] (Sec. 3.1),
+ * i.e. sub-block (a, b) = w_a(r) w_b(c) C with w = [1, xbar], and reduces
+ * again.  Result block rows: FEM vertex v -> v; body b -> the four block
+ * rows n_fem + 4b + {0,1,2,3} (q = [p; a_1; a_2; a_3], a_k the columns of A).
+ * Errors: as gs_assemble, plus GS_ERR_INVALID for a body index out of
+ * range or a body node numbered below n_fem. */
+int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32_t n_bodies,
+                    const int32_t* body_of_node, const double* xbar, const int32_t* rows,
+                    const int32_t* cols, const double* blocks, int64_t n_blocks, gs_mat* out);
+
+/* Size of an assembled matrix: block rows and stored (diagonal + upper) blocks. */
+int gs_mat_info(gs_mat mat, int32_t* n_block_rows, int64_t* nnzb_upper);
+/* Copy the stored blocks out: device int32[nnzb] rid, cid and double[nnzb*9]
+ * au, in ascending (row, col) order.  Any output may be NULL (skipped). */
+int gs_mat_export(gs_ctx ctx, gs_mat mat, int32_t* rid, int32_t* cid, double* au);
+int gs_mat_destroy(gs_mat mat);
+
+/* ---------------------------------------------------------------- SpMV */
+#define GS_SPMV_SRBK 0 /* Alg. SRBK: upper blocks, warp segmented reduce + transposed atomics */
+#define GS_SPMV_ROW 1  /* row-gather over the upper blocks and their transposes; no atomics,
+                          bit-reproducible */
+
+/* y = A x for nrhs right-hand sides (Sec. 5.3), A the full symmetric matrix
+ * whose diagonal and upper blocks `mat` stores.  x, y: device
+ * double[nrhs * 3n], must not overlap.  Errors: GS_ERR_INVALID. */
+int gs_spmv(gs_ctx ctx, gs_mat mat, const double* x, double* y, int32_t nrhs, int32_t variant);
+
+/* ---------------------------------------------------------------- partition */
+/* Level-0 domain partition (Sec. 3.2, Eq. num_subdomains, supplement
+ * Algorithm 1).  Runs on the host, once per mesh, like the paper's METIS
+ * pre-processing.  Rule (deterministic; METIS is replaced): recursive
+ * coordinate bisection of the rest positions -- split a set needing
+ * P = ceil(size / N) > 1 parts along the coordinate of largest extent
+ * (ties: x, then y, then z), ordering by (coordinate, node index) and
+ * putting the first N * ceil(P / 2) nodes left; leaves are parts numbered
+ * left to right, so M = ceil(n_nodes / N) and only the last part is short.
+ * Node v gets slot map[v] = N * part + rank of v in its part (ascending
+ * node index); slots without a node are padding.
+ * X: host double[n_nodes * 3].  map: host int32[n_nodes] (output).
+ * n_domains: host, receives M.  Errors: GS_ERR_INVALID. */
+int gs_partition(int32_t n_nodes, const double* X, int32_t domain_size, int32_t* map,
+                 int32_t* n_domains);
+
+/* ---------------------------------------------------------------- MAS */
+#define GS_PREC_FP64 0 /* domain inverses stored and applied in FP64 */
+#define GS_PREC_FP32 1 /* inverses rounded to FP32, applied with FP32 accumulation */
+
+typedef struct gs_mas_opts {
+  int32_t domain_size; /* N: nodes per domain, 1..32 (paper: 16 or 32, Sec. 3.2) */
+  int32_t max_levels;  /* upper bound on the number of levels, >= 1 */
+  int32_t precision;   /* GS_PREC_* of the stored inverses */
+} gs_mas_opts;
+
+/* Build the connectivity-enhanced MAS preconditioner of `mat` on the
+ * device (Sec. 3.3, Alg. 1; supplement Algorithms 2-5, Eq. 4-6).
+ * map: device int32[n], the level-0 slot of every node (gs_partition);
+ *   n_domains0 level-0 domains of domain_size slots each.
+ * adj_ptr, adj: device int32 CSR of the mesh node graph (n + 1 entries,
+ *   then adj_ptr[n] neighbours); contacts: device int32[2 * n_contacts]
+ *   node pairs (may be NULL when n_contacts == 0).  Edges of both define
+ *   connectivity at every level.
+ * Levels: level l+1's supernodes are the connected components of level
+ * l's items inside each domain, numbered domain by domain and by smallest
+ * lane; a level is added while fewer than max_levels exist, level l has
+ * more than one domain and some items merged.  Level matrices are the
+ * Galerkin products S_d C_l A C_l^T S_d^T; each domain's real part is
+ * inverted through a Cholesky factorisation.
+ * Errors: GS_ERR_INVALID, GS_ERR_UNSUPPORTED (domain_size > 32),
+ * GS_ERR_NOT_SPD (a domain pivot <= 0; no handle is returned). */
+int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_domains0,
+                 const int32_t* adj_ptr, const int32_t* adj, const int32_t* contacts,
+                 int64_t n_contacts, const gs_mas_opts* opts, gs_mas* out);
+
+/* Level count and item counts: n_items[l] for l < *n_levels (n_items may be
+ * NULL; it must hold max_levels entries).  Level 0 counts padded slots. */
+int gs_mas_info(gs_mas mas, int32_t* n_levels, int32_t* n_items);
+/* coarse: device int32[n], the item of every node at `level` (level 0: map). */
+int gs_mas_export_coarse(gs_ctx ctx, gs_mas mas, int32_t level, int32_t* coarse);
+/* inv: device double[n_domains(level) * (3N)^2], each domain's inverse,
+ * row-major 3N x 3N, padded rows/columns zero (FP64 copy). */
+int gs_mas_export_inverse(gs_ctx ctx, gs_mas mas, int32_t level, double* inv);
+/* z = M^{-1} r = sum_l C_l^T M_l^{-1} C_l r (supplement Eq. 6) for nrhs
+ * right-hand sides; r, z device double[nrhs * 3n], not overlapping. */
+int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs);
+int gs_mas_destroy(gs_mas mas);
+
+/* ---------------------------------------------------------------- PCG */
+/* Preconditioned conjugate gradients (Sec. 3.2): x0 = 0, independent
+ * recurrences per right-hand side, stopping RHS k when its recurrence
+ * residual satisfies ||r||_2 <= tol * ||b_k||_2 (b_k = 0 gives x_k = 0 and
+ * 0 iterations) or at max_iter iterations (iteration = one SpMV).
+ * b, x: device double[nrhs * 3n].  iters: host int32[nrhs], rel_res: host
+ * double[nrhs] (recurrence residual ratio at exit); either may be NULL.
+ * spmv_variant: GS_SPMV_*.
+ * Returns GS_OK, GS_ERR_MAXITER (some RHS did not converge; x holds the
+ * last iterate), GS_ERR_NOT_SPD (p.Ap <= 0), GS_ERR_NONFINITE,
+ * GS_ERR_INVALID. */
+int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nrhs, double tol,
+                 int32_t max_iter, int32_t spmv_variant, double* x, int32_t* iters,
+                 double* rel_res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIPC_MAS_PCG_H */

@@ -1,0 +1,293 @@
+"""Thin Python binding of the C ABI in include/gipc_mas_pcg.h.
+
+Functions carry the C names and only marshal arguments: torch CUDA tensors
+become device pointers, numpy arrays host pointers, and a non-zero status
+raises GsError.  Every step of the solve runs in the CUDA library; if the
+library has not been built this module raises instead of falling back.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB_PATH
+
+GS_OK = 0
+GS_ERR_INVALID = -1
+GS_ERR_CUDA = -2
+GS_ERR_NOT_SPD = -3
+GS_ERR_MAXITER = -4
+GS_ERR_NONFINITE = -5
+GS_ERR_UNSUPPORTED = -6
+
+GS_SPMV_SRBK = 0
+GS_SPMV_ROW = 1
+GS_PREC_FP64 = 0
+GS_PREC_FP32 = 1
+
+# Every symbol the header declares (checked by the test-suite).
+EXPORTS = [
+    "gs_status_string",
+    "gs_last_error",
+    "gs_create",
+    "gs_set_stream",
+    "gs_destroy",
+    "gs_assemble",
+    "gs_assemble_abd",
+    "gs_mat_info",
+    "gs_mat_export",
+    "gs_mat_destroy",
+    "gs_spmv",
+    "gs_partition",
+    "gs_build_mas",
+    "gs_mas_info",
+    "gs_mas_export_coarse",
+    "gs_mas_export_inverse",
+    "gs_mas_apply",
+    "gs_mas_destroy",
+    "gs_pcg_solve",
+]
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {_name(status)}: {_last_error()}")
+
+
+class gs_mas_opts(ctypes.Structure):
+    _fields_ = [("domain_size", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing: build it with "
+                "paper_2411_06224_gb300.build.build() (there is no CPU fallback)"
+            )
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "gs_last_error": (ctypes.c_char_p, []),
+            "gs_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+            "gs_set_stream": (ctypes.c_int, [_P, _P]),
+            "gs_destroy": (ctypes.c_int, [_P]),
+            "gs_assemble": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I64, ctypes.POINTER(_P)]),
+            "gs_assemble_abd": (
+                ctypes.c_int,
+                [_P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_P)],
+            ),
+            "gs_mat_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+            "gs_mat_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+            "gs_mat_destroy": (ctypes.c_int, [_P]),
+            "gs_spmv": (ctypes.c_int, [_P, _P, _P, _P, _I32, _I32]),
+            "gs_partition": (ctypes.c_int, [_I32, _P, _I32, _P, ctypes.POINTER(_I32)]),
+            "gs_build_mas": (
+                ctypes.c_int,
+                [_P, _P, _P, _I32, _P, _P, _P, _I64, ctypes.POINTER(gs_mas_opts), ctypes.POINTER(_P)],
+            ),
+            "gs_mas_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), _P]),
+            "gs_mas_export_coarse": (ctypes.c_int, [_P, _P, _I32, _P]),
+            "gs_mas_export_inverse": (ctypes.c_int, [_P, _P, _I32, _P]),
+            "gs_mas_apply": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+            "gs_mas_destroy": (ctypes.c_int, [_P]),
+            "gs_pcg_solve": (ctypes.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _I32, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _name(status):
+    return lib().gs_status_string(status).decode()
+
+
+def _last_error():
+    return lib().gs_last_error().decode()
+
+
+def _check(status, what):
+    if status != GS_OK:
+        raise GsError(status, what)
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- context
+def gs_create(device=0, stream=None):
+    h = _P()
+    with torch.cuda.device(device):
+        _check(lib().gs_create(ctypes.byref(h), device, _stream(stream)), "gs_create")
+    return h
+
+
+def gs_set_stream(ctx, stream=None):
+    _check(lib().gs_set_stream(ctx, _stream(stream)), "gs_set_stream")
+
+
+def gs_destroy(ctx):
+    _check(lib().gs_destroy(ctx), "gs_destroy")
+
+
+# ----------------------------------------------------------------- assembly
+def gs_assemble(ctx, n_block_rows, rows, cols, blocks):
+    """rows, cols: int32 (K,) CUDA; blocks: float64 (K, 3, 3) CUDA.  Returns a gs_mat handle."""
+    h = _P()
+    K = rows.numel()
+    _check(
+        lib().gs_assemble(
+            ctx, n_block_rows, _dev(rows, torch.int32, "rows"), _dev(cols, torch.int32, "cols"),
+            _dev(blocks, torch.float64, "blocks"), K, ctypes.byref(h),
+        ),
+        "gs_assemble",
+    )
+    return h
+
+
+def gs_assemble_abd(ctx, n_nodes, n_fem, n_bodies, body_of_node, xbar, rows, cols, blocks):
+    h = _P()
+    _check(
+        lib().gs_assemble_abd(
+            ctx, n_nodes, n_fem, n_bodies, _dev(body_of_node, torch.int32, "body_of_node"),
+            _dev(xbar, torch.float64, "xbar"), _dev(rows, torch.int32, "rows"), _dev(cols, torch.int32, "cols"),
+            _dev(blocks, torch.float64, "blocks"), rows.numel(), ctypes.byref(h),
+        ),
+        "gs_assemble_abd",
+    )
+    return h
+
+
+def gs_mat_info(mat):
+    n = _I32()
+    nz = _I64()
+    _check(lib().gs_mat_info(mat, ctypes.byref(n), ctypes.byref(nz)), "gs_mat_info")
+    return n.value, nz.value
+
+
+def gs_mat_export(ctx, mat, device="cuda"):
+    """(rid, cid, au) as new CUDA tensors (int32, int32, float64 (U, 3, 3))."""
+    n, nz = gs_mat_info(mat)
+    rid = torch.empty(nz, dtype=torch.int32, device=device)
+    cid = torch.empty(nz, dtype=torch.int32, device=device)
+    au = torch.empty((nz, 3, 3), dtype=torch.float64, device=device)
+    if nz:
+        _check(
+            lib().gs_mat_export(ctx, mat, _dev(rid, torch.int32, "rid"), _dev(cid, torch.int32, "cid"),
+                                _dev(au, torch.float64, "au")),
+            "gs_mat_export",
+        )
+    return rid, cid, au
+
+
+def gs_mat_destroy(mat):
+    _check(lib().gs_mat_destroy(mat), "gs_mat_destroy")
+
+
+# ----------------------------------------------------------------- SpMV
+def gs_spmv(ctx, mat, x, y, nrhs=1, variant=GS_SPMV_ROW):
+    _check(
+        lib().gs_spmv(ctx, mat, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"), nrhs, variant),
+        "gs_spmv",
+    )
+
+
+# ----------------------------------------------------------------- partition / MAS
+def gs_partition(X, domain_size):
+    """Host partition of positions X (V, 3) float64 -> (map int32 (V,), n_domains)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    V = X.shape[0]
+    mp = np.empty(V, dtype=np.int32)
+    nd = _I32()
+    _check(
+        lib().gs_partition(V, X.ctypes.data_as(_P), domain_size, mp.ctypes.data_as(_P), ctypes.byref(nd)),
+        "gs_partition",
+    )
+    return mp, nd.value
+
+
+def gs_build_mas(ctx, mat, map_, n_domains0, adj_ptr, adj, contacts, domain_size=32, max_levels=2,
+                 precision=GS_PREC_FP64):
+    """map_, adj_ptr, adj, contacts: int32 CUDA tensors (contacts (P, 2) or None)."""
+    h = _P()
+    opts = gs_mas_opts(domain_size, max_levels, precision)
+    P = 0 if contacts is None else contacts.shape[0]
+    _check(
+        lib().gs_build_mas(
+            ctx, mat, _dev(map_, torch.int32, "map"), n_domains0, _dev(adj_ptr, torch.int32, "adj_ptr"),
+            _dev(adj, torch.int32, "adj"), _dev(contacts, torch.int32, "contacts") if P else None, P,
+            ctypes.byref(opts), ctypes.byref(h),
+        ),
+        "gs_build_mas",
+    )
+    return h
+
+
+def gs_mas_info(mas):
+    L = _I32()
+    items = (ctypes.c_int32 * 8)()
+    _check(lib().gs_mas_info(mas, ctypes.byref(L), ctypes.cast(items, _P)), "gs_mas_info")
+    return L.value, [items[i] for i in range(L.value)]
+
+
+def gs_mas_export_coarse(ctx, mas, level, n, device="cuda"):
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    _check(lib().gs_mas_export_coarse(ctx, mas, level, _dev(out, torch.int32, "coarse")), "gs_mas_export_coarse")
+    return out
+
+
+def gs_mas_export_inverse(ctx, mas, level, n_domains, domain_size, device="cuda"):
+    ld = 3 * domain_size
+    out = torch.empty((n_domains, ld, ld), dtype=torch.float64, device=device)
+    _check(lib().gs_mas_export_inverse(ctx, mas, level, _dev(out, torch.float64, "inv")), "gs_mas_export_inverse")
+    return out
+
+
+def gs_mas_apply(ctx, mas, r, z, nrhs=1):
+    _check(lib().gs_mas_apply(ctx, mas, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z"), nrhs),
+           "gs_mas_apply")
+
+
+def gs_mas_destroy(mas):
+    _check(lib().gs_mas_destroy(mas), "gs_mas_destroy")
+
+
+# ----------------------------------------------------------------- PCG
+def gs_pcg_solve(ctx, mat, mas, b, x, nrhs=1, tol=1e-6, max_iter=10_000, variant=GS_SPMV_ROW,
+                 raise_on_maxiter=True):
+    """Solve A x = b for nrhs stacked right-hand sides; returns (iters, rel_res, status)."""
+    iters = np.zeros(nrhs, dtype=np.int32)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    s = lib().gs_pcg_solve(
+        ctx, mat, mas, _dev(b, torch.float64, "b"), nrhs, tol, max_iter, variant, _dev(x, torch.float64, "x"),
+        iters.ctypes.data_as(_P), rel.ctypes.data_as(_P),
+    )
+    if s != GS_OK and not (s == GS_ERR_MAXITER and not raise_on_maxiter):
+        raise GsError(s, "gs_pcg_solve")
+    return iters, rel, s

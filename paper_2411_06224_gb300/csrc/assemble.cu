@@ -1,0 +1,233 @@
+// Global Hessian assembly by hash-key reduction (Sec. 5.1-5.2).
+//
+// FastHashReduction: encode every consumed (row <= col) block with a key,
+// radix-sort (key, input index) pairs so duplicates become adjacent, mark
+// P[i] = K[i] != K[i+1], take O = ExclusiveSum(P) as each entry's unique-key
+// index, and reduce runs with FastSegmentReduction (a warp head-segmented
+// reduction; segments crossing a warp boundary finish with atomics).
+//
+// GB300 choices: keys are packed as (row << b) | col with b the bit width
+// of n, which keeps the (row, col) order of the paper's (row << 32) | col
+// encoding while shortening the radix sort to 2b bits; values are gathered
+// through the sorted index instead of being sorted along (72-byte payloads
+// are read once, in the reduction).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "common.cuh"
+#include "primitives.cuh"
+
+namespace gs {
+
+__global__ void k_encode_keys(const int32_t* __restrict__ rows, const int32_t* __restrict__ cols, int64_t nb,
+                              int32_t n, int shift, uint64_t sentinel, uint64_t* __restrict__ keys,
+                              uint32_t* __restrict__ idx, int* flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int32_t r = rows[i], c = cols[i];
+  uint64_t key = sentinel;
+  if (r < 0 || r >= n || c < 0 || c >= n) {
+    atomicOr(flags, kErrIndex);
+  } else if (r <= c) {
+    key = ((uint64_t)r << shift) | (uint64_t)c;
+  }
+  keys[i] = key;
+  idx[i] = (uint32_t)i;
+}
+
+// P[i] = K[i] != K[i+1]; the last entry closes the final run.
+__global__ void k_run_flags(const uint64_t* __restrict__ keys, int64_t nb, int32_t* __restrict__ P) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  P[i] = (i + 1 == nb) ? 1 : (keys[i] != keys[i + 1]);
+}
+
+// FastSegmentReduction over the sorted entries.  Thread i holds the block
+// of sorted entry i (gathered through idx) and its unique-key index O[i].
+// The first entry of each run also writes the decoded (row, col).
+__global__ void k_fast_segment_reduce(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
+                                      const int32_t* __restrict__ O, const double* __restrict__ blocks,
+                                      int64_t nb, uint64_t sentinel, int shift, double* __restrict__ R,
+                                      int32_t* __restrict__ rid, int32_t* __restrict__ cid) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  bool in = i < nb;
+  uint64_t key = in ? keys[i] : sentinel;
+  bool valid = in && key != sentinel;
+  int32_t b = in ? O[i] : -1;
+  int32_t b_prev = (in && i > 0) ? O[i - 1] : -1;
+  bool head = (lane == 0) || (b_prev != b);
+  double v[9];
+  if (valid) {
+    const double* src = blocks + (size_t)idx[i] * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = src[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = 0.0;
+  }
+  unsigned hm = __ballot_sync(kFull, head);
+  int send = segment_end(hm, lane);
+  head_segmented_reduce<9>(v, lane, send);
+  if (!valid) return;
+  if (b_prev != b) {  // first entry of its run: record the key
+    rid[b] = (int32_t)(key >> shift);
+    cid[b] = (int32_t)(key & ((1ull << shift) - 1));
+  }
+  if (!head) return;
+  // A segment that began in an earlier warp or continues into the next one
+  // is shared between warps: finish it with atomics; otherwise store.
+  bool cont_prev = (lane == 0) && (b_prev == b);
+  bool cont_next = false;
+  if (send == 32) {
+    int64_t nxt = i - lane + 32;
+    cont_next = nxt < nb && O[nxt] == b;
+  }
+  double* dst = R + (size_t)b * 9;
+  if (cont_prev || cont_next) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(dst + k, v[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dst[k] = v[k];
+  }
+}
+
+// row_ptr[r] = first stored block of row r (rows without blocks get the
+// next row's start); row_ptr[n] = U.
+__global__ void k_row_ptr(const int32_t* __restrict__ rid, int64_t U, int32_t n, int32_t* __restrict__ row_ptr) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u > U) return;
+  int32_t r_here = (u < U) ? rid[u] : n;
+  int32_t r_prev = (u > 0) ? rid[u - 1] : -1;
+  for (int32_t r = r_prev + 1; r <= r_here; ++r) row_ptr[r] = (int32_t)u;
+}
+
+// Reduce (rows, cols, blocks) to a new matrix.  Shared by gs_assemble and
+// the second level of gs_assemble_abd.
+int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* cols, const double* blocks,
+                  int64_t nb, gs_mat* out) {
+  cudaStream_t st = ctx->stream;
+  gs_mat m = new gs_mat_s();
+  m->n = n;
+  m->owner = ctx;
+  const int shift = bits_for(n);
+  const uint64_t sentinel = (shift * 2 >= 64) ? ~0ull : ((1ull << (2 * shift)) - 1);
+  const int end_bit = 2 * shift;
+  uint64_t *k_in = nullptr, *k_out = nullptr;
+  uint32_t *i_in = nullptr, *i_out = nullptr;
+  int32_t *P = nullptr, *O = nullptr;
+  int64_t U = 0;
+  auto fail = [&](int s) {
+    gs_mat_destroy(m);
+    return s;
+  };
+  if (nb > 0) {
+    int s;
+    if ((s = ctx->scratch_buf(kSlotSortKeysIn, nb * 8, (void**)&k_in)) ||
+        (s = ctx->scratch_buf(kSlotSortKeysOut, nb * 8, (void**)&k_out)) ||
+        (s = ctx->scratch_buf(kSlotSortValsIn, nb * 4, (void**)&i_in)) ||
+        (s = ctx->scratch_buf(kSlotSortValsOut, nb * 4, (void**)&i_out)) ||
+        (s = ctx->scratch_buf(kSlotScan, nb * 8, (void**)&P)))
+      return fail(s);
+    O = P + nb;
+    const int T = 256;
+    k_encode_keys<<<ceil_div(nb, T), T, 0, st>>>(rows, cols, nb, n, shift, sentinel, k_in, i_in, ctx->d_flags);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0, end_bit, st);
+    void* temp = nullptr;
+    if ((s = ctx->scratch_buf(kSlotSortTemp, tb, &temp))) return fail(s);
+    if (cudaSuccess != cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0,
+                                                       end_bit, st)) {
+      set_error("radix sort failed");
+      return fail(GS_ERR_CUDA);
+    }
+    k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(k_out, nb, P);
+    size_t sb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, sb, P, O, (int64_t)nb, st);
+    if ((s = ctx->scratch_buf(kSlotSortTemp, std::max(sb, tb), &temp))) return fail(s);
+    cub::DeviceScan::ExclusiveSum(temp, sb, P, O, (int64_t)nb, st);
+    // U = distinct keys, minus the sentinel group if present.
+    uint64_t* hk = (uint64_t*)ctx->h_pinned;
+    int32_t* ho = (int32_t*)(ctx->h_pinned + 4);
+    if (cudaMemcpyAsync(hk, k_out + nb - 1, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(ho, O + nb - 1, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("assembly readback failed");
+      return fail(GS_ERR_CUDA);
+    }
+    U = (int64_t)ho[0] + 1 - (hk[0] == sentinel ? 1 : 0);
+  }
+  int flags = 0;
+  GS_TRY(ctx->take_flags(&flags));
+  if (flags) return fail(status_from_flags(flags));
+  m->nnzb = U;
+  int s;
+  if ((s = ctx->alloc((void**)&m->au, (size_t)U * 9 * sizeof(double))) ||
+      (s = ctx->alloc((void**)&m->rid, (size_t)U * 4)) || (s = ctx->alloc((void**)&m->cid, (size_t)U * 4)) ||
+      (s = ctx->alloc((void**)&m->row_ptr, (size_t)(n + 1) * 4)))
+    return fail(s);
+  if (U > 0) {
+    if (cudaMemsetAsync(m->au, 0, (size_t)U * 9 * sizeof(double), st) != cudaSuccess) return fail(GS_ERR_CUDA);
+    const int T = 256;
+    k_fast_segment_reduce<<<ceil_div(nb, T), T, 0, st>>>(k_out, i_out, O, blocks, nb, sentinel, shift, m->au,
+                                                            m->rid, m->cid);
+  }
+  k_row_ptr<<<ceil_div(U + 1, 256), 256, 0, st>>>(m->rid, U, n, m->row_ptr);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("assembly kernel launch failed");
+    return fail(GS_ERR_CUDA);
+  }
+  *out = m;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+int gs_assemble(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* cols, const double* blocks,
+                int64_t nb, gs_mat* out) {
+  GS_CHECK(ctx && out, GS_ERR_INVALID, "gs_assemble: null context or output");
+  *out = nullptr;
+  GS_CHECK(n > 0 && n < (1 << 30), GS_ERR_INVALID, "gs_assemble: n_block_rows %d out of range", n);
+  GS_CHECK(nb >= 0 && nb < (1LL << 31), GS_ERR_INVALID, "gs_assemble: n_blocks %lld out of range", (long long)nb);
+  GS_CHECK(nb == 0 || (rows && cols && blocks), GS_ERR_INVALID, "gs_assemble: null input");
+  GS_CUDA(cudaSetDevice(ctx->device));
+  return reduce_blocks(ctx, n, rows, cols, blocks, nb, out);
+}
+
+int gs_mat_info(gs_mat m, int32_t* n, int64_t* nnzb) {
+  GS_CHECK(m, GS_ERR_INVALID, "gs_mat_info: null matrix");
+  if (n) *n = m->n;
+  if (nnzb) *nnzb = m->nnzb;
+  return GS_OK;
+}
+
+int gs_mat_export(gs_ctx ctx, gs_mat m, int32_t* rid, int32_t* cid, double* au) {
+  GS_CHECK(ctx && m, GS_ERR_INVALID, "gs_mat_export: null argument");
+  cudaStream_t st = ctx->stream;
+  if (m->nnzb == 0) return GS_OK;
+  if (rid) GS_CUDA(cudaMemcpyAsync(rid, m->rid, m->nnzb * 4, cudaMemcpyDeviceToDevice, st));
+  if (cid) GS_CUDA(cudaMemcpyAsync(cid, m->cid, m->nnzb * 4, cudaMemcpyDeviceToDevice, st));
+  if (au) GS_CUDA(cudaMemcpyAsync(au, m->au, m->nnzb * 72, cudaMemcpyDeviceToDevice, st));
+  return GS_OK;
+}
+
+int gs_mat_destroy(gs_mat m) {
+  if (!m) return GS_OK;
+  gs_ctx c = m->owner;
+  c->release(m->au);
+  c->release(m->rid);
+  c->release(m->cid);
+  c->release(m->row_ptr);
+  c->release(m->lo_ptr);
+  c->release(m->lo_idx);
+  c->release(m->lo_col);
+  delete m;
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gipc_mas_pcg.h"
+
+namespace gs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+
+#define GS_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::gs::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return GS_ERR_CUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
+
+#define GS_CHECK(cond, status, ...) \
+  do {                              \
+    if (!(cond)) {                  \
+      ::gs::set_error(__VA_ARGS__); \
+      return (status);              \
+    }                               \
+  } while (0)
+
+#define GS_TRY(expr)         \
+  do {                       \
+    int s_ = (expr);         \
+    if (s_ != GS_OK) return s_; \
+  } while (0)
+
+// Device-side error flags (bitwise OR of these) written by kernels that
+// validate their inputs; the host reads the word at the next sync point.
+enum : int {
+  kErrIndex = 1,      // an index out of range
+  kErrNotSPD = 2,     // non-positive Cholesky pivot / p.Ap <= 0
+  kErrNonFinite = 4,  // NaN / Inf in a reduction
+};
+
+int status_from_flags(int flags);
+
+// ------------------------------------------------------------------ memory
+// A grow-only device buffer from the stream-ordered pool.
+struct Buffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gs
+
+struct gs_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int* d_flags = nullptr;     // device error word
+  int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
+  std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls
+
+  // Stream-ordered allocation on this context's stream.
+  int alloc(void** p, size_t bytes);
+  void release(void* p);
+  // Scratch slot `slot` with at least `bytes` bytes (contents undefined).
+  int scratch_buf(int slot, size_t bytes, void** p);
+  // Read and clear the device error word (synchronises the stream).
+  int take_flags(int* flags);
+  int sync();
+};
+
+namespace gs {
+
+// Scratch slot ids (each a separate grow-only buffer in the context).
+enum ScratchSlot : int {
+  kSlotSortKeysIn = 0,
+  kSlotSortKeysOut,
+  kSlotSortValsIn,
+  kSlotSortValsOut,
+  kSlotSortTemp,
+  kSlotScan,
+  kSlotReduce,
+  kSlotPcgVectors,
+  kSlotPcgScalars,
+  kSlotMasLevelVec,
+  kSlotMasBuild0,
+  kSlotMasBuild1,
+  kSlotMasBuild2,
+  kSlotMasBuild3,
+  kSlotCount
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Number of bits needed to write values 0..n (inclusive).
+inline int bits_for(long long n) {
+  int b = 0;
+  while ((1LL << b) <= n) ++b;
+  return b;
+}
+
+}  // namespace gs
+
+struct gs_mat_s {
+  int32_t n = 0;        // block rows
+  int64_t nnzb = 0;     // stored diagonal + upper blocks
+  int32_t* rid = nullptr;
+  int32_t* cid = nullptr;
+  double* au = nullptr;       // nnzb * 9, row-major blocks
+  int32_t* row_ptr = nullptr; // n + 1, over the sorted upper blocks
+  // Transposed references for the row-gather SpMV (built lazily):
+  // for block row r, the stored blocks (c, r) with c < r, as indices into au.
+  int32_t* lo_ptr = nullptr;  // n + 1
+  int32_t* lo_idx = nullptr;  // nnzb - n_diag
+  int32_t* lo_col = nullptr;  // the c of each such block
+  gs_ctx owner = nullptr;
+};
+
+struct gs_mas_s {
+  int32_t N = 0;          // domain size
+  int32_t n = 0;          // fine nodes
+  int32_t L = 0;          // levels
+  int32_t precision = 0;
+  std::vector<int32_t> n_items;    // per level (level 0: padded slots)
+  std::vector<int32_t> n_domains;  // per level
+  std::vector<int32_t*> coarse;    // per level: device int32[n] (level 0 = map)
+  int32_t* remap0 = nullptr;       // device int32[n_items[0]], slot -> node or -1
+  std::vector<double*> inv64;      // per level: n_domains * (3N)^2
+  std::vector<float*> inv32;       // per level (FP32 precision only)
+  std::vector<int64_t> vec_off;    // per level l >= 1: offset (in items) into the multilevel vector
+  int64_t vec_items = 0;           // total items of levels >= 1
+  void** d_inv_tab = nullptr;      // device table: inverse pointer per level (FP64 or FP32)
+  int32_t* d_coarse_jobs = nullptr;  // device: level then domain of every coarse-level domain
+  int32_t n_coarse_jobs = 0;
+  gs_ctx owner = nullptr;
+};

@@ -1,0 +1,144 @@
+// Context, errors and stream-ordered memory.
+#include <cstdarg>
+
+#include "common.cuh"
+
+namespace gs {
+
+static thread_local char g_last_error[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+int status_from_flags(int flags) {
+  if (flags & kErrIndex) {
+    set_error("an input index is out of range");
+    return GS_ERR_INVALID;
+  }
+  if (flags & kErrNotSPD) {
+    set_error("matrix or preconditioner is not positive definite");
+    return GS_ERR_NOT_SPD;
+  }
+  if (flags & kErrNonFinite) {
+    set_error("non-finite value in a reduction");
+    return GS_ERR_NONFINITE;
+  }
+  return GS_OK;
+}
+
+}  // namespace gs
+
+int gs_ctx_s::alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return GS_OK;
+  GS_CUDA(cudaMallocAsync(p, bytes, stream));
+  return GS_OK;
+}
+
+void gs_ctx_s::release(void* p) {
+  if (p) cudaFreeAsync(p, stream);
+}
+
+int gs_ctx_s::scratch_buf(int slot, size_t bytes, void** p) {
+  if ((int)scratch.size() <= slot) scratch.resize(slot + 1);
+  gs::Buffer& b = scratch[slot];
+  if (b.bytes < bytes) {
+    release(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8 + 256;
+    GS_TRY(alloc(&b.ptr, want));
+    b.bytes = want;
+  }
+  *p = b.ptr;
+  return GS_OK;
+}
+
+int gs_ctx_s::take_flags(int* flags) {
+  GS_CUDA(cudaMemcpyAsync(h_pinned, d_flags, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  *flags = h_pinned[0];
+  return GS_OK;
+}
+
+int gs_ctx_s::sync() {
+  GS_CUDA(cudaStreamSynchronize(stream));
+  return GS_OK;
+}
+
+extern "C" {
+
+const char* gs_status_string(int s) {
+  switch (s) {
+    case GS_OK: return "GS_OK";
+    case GS_ERR_INVALID: return "GS_ERR_INVALID";
+    case GS_ERR_CUDA: return "GS_ERR_CUDA";
+    case GS_ERR_NOT_SPD: return "GS_ERR_NOT_SPD";
+    case GS_ERR_MAXITER: return "GS_ERR_MAXITER";
+    case GS_ERR_NONFINITE: return "GS_ERR_NONFINITE";
+    case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+    default: return "GS_ERR_UNKNOWN";
+  }
+}
+
+const char* gs_last_error(void) { return gs::g_last_error; }
+
+int gs_create(gs_ctx* out, int device, void* stream) {
+  GS_CHECK(out != nullptr, GS_ERR_INVALID, "gs_create: out is null");
+  *out = nullptr;
+  int count = 0;
+  GS_CUDA(cudaGetDeviceCount(&count));
+  GS_CHECK(device >= 0 && device < count, GS_ERR_INVALID, "gs_create: device %d of %d", device, count);
+  GS_CUDA(cudaSetDevice(device));
+  gs_ctx c = new gs_ctx_s();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete c;
+    gs::set_error("gs_create: cudaGetDeviceProperties failed");
+    return GS_ERR_CUDA;
+  }
+  c->sm_count = prop.multiProcessorCount;
+  // Keep freed pool memory cached by the pool instead of returning it to
+  // the driver at every synchronisation.
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (cudaMalloc(&c->d_flags, 256) != cudaSuccess || cudaMallocHost(&c->h_pinned, 4096) != cudaSuccess ||
+      cudaMemset(c->d_flags, 0, 256) != cudaSuccess) {
+    gs::set_error("gs_create: allocation failed");
+    if (c->d_flags) cudaFree(c->d_flags);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+    return GS_ERR_CUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+int gs_set_stream(gs_ctx ctx, void* stream) {
+  GS_CHECK(ctx != nullptr, GS_ERR_INVALID, "gs_set_stream: null context");
+  ctx->stream = (cudaStream_t)stream;
+  return GS_OK;
+}
+
+int gs_destroy(gs_ctx ctx) {
+  if (!ctx) return GS_OK;
+  cudaSetDevice(ctx->device);
+  for (auto& b : ctx->scratch) ctx->release(b.ptr);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_flags);
+  cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// MAS preconditioner apply z = sum_l C_l^T M_l^{-1} C_l r (supplement Eq. 4-6).
+//
+// The coarseners map level 0 directly to every level, so all levels are
+// independent once the restricted vectors exist:
+//   1. k_restrict: one warp per level-0 domain gathers its nodes' residuals
+//      and sums them per coarse item (usually one item per domain: one warp
+//      reduction and one atomic per component), for every level >= 1;
+//   2. k_domain_product on the coarse levels: z_l = M_l^{-1} r_l per domain;
+//   3. k_domain_product on level 0 fused with the prolongation: each node's
+//      z = (M_0^{-1} r)_slot + sum_l z_l[coarse_l(node)], written once.
+// The dense products read each inverse once for all right-hand sides: a
+// thread owns one row of the 3N x 3N inverse and kRPT right-hand sides;
+// the inverse is symmetric, so row i is read as column i (coalesced).
+#include "common.cuh"
+#include "primitives.cuh"
+
+namespace gs {
+
+struct ApplyLevels {
+  const int32_t* coarse[8];
+  int64_t vec_off[8];
+  int L;
+  int N;
+};
+
+__global__ void k_restrict(const double* __restrict__ r, int64_t stride, int nrhs, const int32_t* __restrict__ remap0,
+                           int32_t n_dom0, ApplyLevels al, double* __restrict__ rl, int64_t lstride) {
+  int32_t d = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (d >= n_dom0) return;
+  const int N = al.N;
+  int32_t node = lane < N ? remap0[(int64_t)d * N + lane] : -1;
+  const bool real = node >= 0;
+  for (int l = 1; l < al.L; ++l) {
+    const int32_t c = real ? al.coarse[l][node] : -1;
+    uint32_t left = __ballot_sync(kFull, real);
+    while (left) {
+      const int lead = __ffs(left) - 1;
+      const int32_t cc = __shfl_sync(kFull, c, lead);
+      const uint32_t g = __ballot_sync(kFull, real && c == cc);
+      left &= ~g;
+      const bool mine = (g >> lane) & 1u;
+      for (int k = 0; k < nrhs; ++k) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          double v = mine ? r[k * stride + 3 * (int64_t)node + x] : 0.0;
+          v = warp_sum(v);
+          if (lane == 0) atomicAdd(&rl[k * lstride + 3 * (al.vec_off[l] + cc) + x], v);
+        }
+      }
+    }
+  }
+}
+
+// Dense per-domain products.  kMode 0: coarse levels (input rl, output zl);
+// kMode 1: level 0 (gather through remap0, prolongate, write z).
+template <typename Tm, int kRPT, int kMode>
+__global__ void __launch_bounds__(1024) k_domain_product(
+    const Tm* const* __restrict__ inv, const int32_t* __restrict__ job_level, const int32_t* __restrict__ job_dom,
+    int N, int nrhs,
+    // level-0 inputs / outputs
+    const double* __restrict__ r, double* __restrict__ z, int64_t stride, const int32_t* __restrict__ remap0,
+    // multilevel vectors
+    const double* __restrict__ rl, double* __restrict__ zl, int64_t lstride, ApplyLevels al) {
+  extern __shared__ unsigned char smem_raw[];
+  Tm* sr = (Tm*)smem_raw;  // [3N][nrhs]
+  const int ld = 3 * N;
+  const int l = (kMode == 1) ? 0 : job_level[blockIdx.x];
+  const int32_t d = (kMode == 1) ? blockIdx.x : job_dom[blockIdx.x];
+  const Tm* Mi = inv[l] + (int64_t)d * ld * ld;
+  const int tid = threadIdx.x;
+  // stage the domain's right-hand sides
+  for (int e = tid; e < ld * nrhs; e += blockDim.x) {
+    const int j = e / nrhs, k = e % nrhs;
+    double v;
+    if (kMode == 1) {
+      const int32_t node = remap0[(int64_t)d * N + j / 3];
+      v = node >= 0 ? r[k * stride + 3 * (int64_t)node + j % 3] : 0.0;
+    } else {
+      v = rl[k * lstride + 3 * (al.vec_off[l] + (int64_t)d * N) + j];
+    }
+    sr[j * nrhs + k] = (Tm)v;
+  }
+  __syncthreads();
+  const int i = tid % ld;
+  const int g = tid / ld;
+  const int k0 = g * kRPT;
+  if (k0 >= nrhs) return;
+  Tm acc[kRPT];
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) acc[q] = (Tm)0;
+  for (int j = 0; j < ld; ++j) {
+    const Tm m = Mi[(int64_t)j * ld + i];
+    const Tm* rj = sr + j * nrhs + k0;
+#pragma unroll
+    for (int q = 0; q < kRPT; ++q)
+      if (k0 + q < nrhs) acc[q] += m * rj[q];
+  }
+  if (kMode == 0) {
+#pragma unroll
+    for (int q = 0; q < kRPT; ++q)
+      if (k0 + q < nrhs) zl[(k0 + q) * lstride + 3 * (al.vec_off[l] + (int64_t)d * N) + i] = (double)acc[q];
+    return;
+  }
+  const int32_t node = remap0[(int64_t)d * N + i / 3];
+  if (node < 0) return;
+  const int x = i % 3;
+  int32_t citem[8];
+  for (int ll = 1; ll < al.L; ++ll) citem[ll] = al.coarse[ll][node];
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) {
+    const int k = k0 + q;
+    if (k >= nrhs) break;
+    double v = (double)acc[q];
+    for (int ll = 1; ll < al.L; ++ll) v += zl[k * lstride + 3 * (al.vec_off[ll] + citem[ll]) + x];
+    z[k * stride + 3 * (int64_t)node + x] = v;
+  }
+}
+
+template <typename Tm>
+static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const int32_t* d_jobs, int n_coarse_jobs,
+                        const double* r, double* z, int nrhs, double* rl, double* zl) {
+  cudaStream_t st = ctx->stream;
+  const int N = mas->N, ld = 3 * N;
+  const int64_t stride = 3LL * mas->n;
+  const int64_t lstride = 3 * std::max<int64_t>(mas->vec_items, 1);
+  ApplyLevels al{};
+  al.L = mas->L;
+  al.N = N;
+  for (int l = 0; l < mas->L; ++l) {
+    al.coarse[l] = mas->coarse[l];
+    al.vec_off[l] = mas->vec_off[l];
+  }
+  constexpr int kRPT = 4;
+  const int groups = ceil_div(nrhs, kRPT);
+  const int threads = ((ld * groups + 31) / 32) * 32;
+  const size_t smem = (size_t)ld * nrhs * sizeof(Tm);
+  GS_CHECK(threads <= 1024, GS_ERR_UNSUPPORTED, "mas apply: too many right-hand sides (%d)", nrhs);
+  if (mas->L > 1) {
+    GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
+    k_restrict<<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(r, stride, nrhs, mas->remap0,
+                                                                              mas->n_domains[0], al, rl, lstride);
+    k_domain_product<Tm, kRPT, 0><<<n_coarse_jobs, threads, smem, st>>>(
+        d_inv, d_jobs, d_jobs + n_coarse_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al);
+  }
+  k_domain_product<Tm, kRPT, 1><<<mas->n_domains[0], threads, smem, st>>>(d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride,
+                                                                         mas->remap0, rl, zl, lstride, al);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl) {
+  if (mas->precision == GS_PREC_FP32)
+    return launch_apply<float>(ctx, mas, (const float* const*)mas->d_inv_tab, mas->d_coarse_jobs,
+                               mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+  return launch_apply<double>(ctx, mas, (const double* const*)mas->d_inv_tab, mas->d_coarse_jobs,
+                              mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+}
+
+int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl) {
+  const size_t per = (size_t)nrhs * 3 * std::max<int64_t>(mas->vec_items, 1);
+  double* b = nullptr;
+  GS_TRY(ctx->scratch_buf(kSlotMasLevelVec, 2 * per * sizeof(double), (void**)&b));
+  *rl = b;
+  *zl = b + per;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs) {
+  GS_CHECK(ctx && mas && r && z && r != z, GS_ERR_INVALID, "gs_mas_apply: null or aliased argument");
+  GS_CHECK(nrhs >= 1, GS_ERR_INVALID, "gs_mas_apply: nrhs %d", nrhs);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  double *rl, *zl;
+  GS_TRY(gs::mas_level_vectors(ctx, mas, nrhs, &rl, &zl));
+  return gs::mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl);
+}

@@ -1,0 +1,258 @@
+// Preconditioned conjugate gradients for several right-hand sides (Sec. 3.2).
+//
+// Per iteration (one SpMV per RHS):
+//   Ap = A p                         spmv.cu
+//   alpha = rz / (p . Ap)            k_dot (finalised on the device)
+//   x += alpha p, r -= alpha Ap      k_update_xr, fused with ||r||^2 and the
+//                                    per-RHS convergence test
+//   z = M^{-1} r                     mas_apply.cu
+//   beta = (r . z) / rz, rz = r . z  k_dot
+//   p = z + beta p                   k_update_p
+// Every reduction is deterministic: a fixed grid writes per-block partials
+// and the last block to finish sums them in block order and updates the
+// per-RHS scalars, so no scalar ever travels to the host inside the loop.
+// A RHS stops moving once converged (alpha = 0), which keeps each RHS on
+// exactly its own single-RHS recurrence.  Kernels return at once after
+// every RHS converged; the host only polls that flag every few iterations.
+#include <cmath>
+
+#include "common.cuh"
+#include "primitives.cuh"
+
+namespace gs {
+
+int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant);
+int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl);
+int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl);
+int ensure_lower(gs_ctx ctx, gs_mat m);
+
+constexpr int kMaxRhs = 32;
+constexpr int kRedBlocks = 296;  // fixed grid of the reductions (2 per SM on 148+ SMs)
+constexpr int kRedThreads = 256;
+
+struct PcgScalars {
+  double bnorm2[kMaxRhs];
+  double rz[kMaxRhs];
+  double alpha[kMaxRhs];
+  double beta[kMaxRhs];
+  double rr[kMaxRhs];
+  int conv[kMaxRhs];
+  int iters[kMaxRhs];
+  int all_conv;
+  unsigned counter;
+  int flags;
+};
+
+enum DotOp : int { kOpBnorm = 0, kOpRzInit, kOpPAp, kOpRR, kOpRz };
+
+// Block-level sum of nrhs values per thread into partials[block][k].
+__device__ __forceinline__ void block_partials(double (&v)[kMaxRhs], int nrhs, double* __restrict__ partials) {
+  __shared__ double red[kRedThreads / 32][kMaxRhs];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < nrhs; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) red[w][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) s += red[q][threadIdx.x];
+    partials[blockIdx.x * kMaxRhs + threadIdx.x] = s;
+  }
+}
+
+// Last block: sum partials in block order and apply op to the scalars.
+__device__ void finalize(PcgScalars* s, const double* __restrict__ partials, int nrhs, int op, double tol2) {
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicInc(&s->counter, gridDim.x - 1) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    const int k = threadIdx.x;
+    double sum = 0.0;
+    if (k < nrhs)
+      for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile const double*)partials)[b * kMaxRhs + k];
+    bool conv_k = true;
+    if (k < nrhs) {
+      if (!isfinite(sum)) {
+        atomicOr(&s->flags, kErrNonFinite);
+        s->conv[k] = 1;
+      } else if (op == kOpBnorm) {
+        s->bnorm2[k] = sum;
+        s->conv[k] = sum == 0.0;
+        s->iters[k] = 0;
+        s->rr[k] = sum;
+      } else if (op == kOpRzInit) {
+        s->rz[k] = sum;
+      } else if (op == kOpPAp) {
+        if (!s->conv[k]) {
+          if (!(sum > 0.0)) {
+            atomicOr(&s->flags, kErrNotSPD);
+            s->conv[k] = 1;
+            s->alpha[k] = 0.0;
+          } else {
+            s->alpha[k] = s->rz[k] / sum;
+          }
+        } else {
+          s->alpha[k] = 0.0;
+        }
+      } else if (op == kOpRR) {
+        if (!s->conv[k]) {
+          s->rr[k] = sum;
+          s->iters[k] += 1;
+          if (sum <= tol2 * s->bnorm2[k]) s->conv[k] = 1;
+        }
+      } else if (op == kOpRz) {
+        s->beta[k] = s->conv[k] ? 0.0 : sum / s->rz[k];
+        s->rz[k] = sum;
+      }
+      conv_k = s->conv[k] != 0;
+    }
+    const bool all = __all_sync(kFull, conv_k);
+    if (k == 0 && (op == kOpRR || op == kOpBnorm || op == kOpPAp)) s->all_conv = all ? 1 : 0;
+  }
+}
+
+// Generic dot a_k . b_k for all RHS; kCopy also writes dst = b (p = z).
+template <bool kCopy>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const double* __restrict__ a, const double* __restrict__ b,
+                                                     double* __restrict__ dst, int64_t len, int nrhs,
+                                                     PcgScalars* s, double* __restrict__ partials, int op) {
+  if (s->all_conv && op != kOpBnorm && op != kOpRzInit) return;
+  double v[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) v[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nrhs; ++k) {
+      double bb = b[k * len + i];
+      v[k] += a[k * len + i] * bb;
+      if (kCopy) dst[k * len + i] = bb;
+    }
+  }
+  block_partials(v, nrhs, partials);
+  finalize(s, partials, nrhs, op, 0.0);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_init(const double* __restrict__ bvec, double* __restrict__ x,
+                                                      double* __restrict__ r, int64_t len, int nrhs, PcgScalars* s,
+                                                      double* __restrict__ partials) {
+  double v[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) v[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nrhs; ++k) {
+      double bb = bvec[k * len + i];
+      x[k * len + i] = 0.0;
+      r[k * len + i] = bb;
+      v[k] += bb * bb;
+    }
+  }
+  block_partials(v, nrhs, partials);
+  finalize(s, partials, nrhs, kOpBnorm, 0.0);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(double* __restrict__ x, double* __restrict__ r,
+                                                           const double* __restrict__ p, const double* __restrict__ Ap,
+                                                           int64_t len, int nrhs, PcgScalars* s,
+                                                           double* __restrict__ partials, double tol2) {
+  if (s->all_conv) return;
+  double v[kMaxRhs];
+  double al[kMaxRhs];
+  for (int k = 0; k < nrhs; ++k) v[k] = 0.0, al[k] = s->alpha[k];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nrhs; ++k) {
+      const int64_t o = k * len + i;
+      double rk = r[o];
+      if (al[k] != 0.0) {
+        x[o] += al[k] * p[o];
+        rk -= al[k] * Ap[o];
+        r[o] = rk;
+      }
+      v[k] += rk * rk;
+    }
+  }
+  block_partials(v, nrhs, partials);
+  finalize(s, partials, nrhs, kOpRR, tol2);
+}
+
+__global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, int64_t len, int nrhs,
+                           const PcgScalars* s) {
+  if (s->all_conv) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nrhs; ++k) {
+      if (s->conv[k]) continue;
+      const int64_t o = k * len + i;
+      p[o] = z[o] + s->beta[k] * p[o];
+    }
+  }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nrhs, double tol,
+                            int32_t max_iter, int32_t variant, double* x, int32_t* iters, double* rel_res) {
+  GS_CHECK(ctx && mat && mas && b && x, GS_ERR_INVALID, "gs_pcg_solve: null argument");
+  GS_CHECK(nrhs >= 1 && nrhs <= kMaxRhs, GS_ERR_INVALID, "gs_pcg_solve: nrhs %d (1..%d)", nrhs, kMaxRhs);
+  GS_CHECK(mas->n == mat->n, GS_ERR_INVALID, "gs_pcg_solve: preconditioner built for another size");
+  GS_CHECK(tol >= 0.0 && max_iter >= 0, GS_ERR_INVALID, "gs_pcg_solve: tol %g max_iter %d", tol, max_iter);
+  GS_CHECK(variant == GS_SPMV_SRBK || variant == GS_SPMV_ROW, GS_ERR_INVALID, "gs_pcg_solve: variant %d", variant);
+  GS_CHECK(b != x, GS_ERR_INVALID, "gs_pcg_solve: b and x alias");
+  GS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const int64_t len = 3LL * mat->n;
+  const size_t vbytes = (size_t)nrhs * len * sizeof(double);
+  double* vec = nullptr;
+  GS_TRY(ctx->scratch_buf(kSlotPcgVectors, 4 * vbytes, (void**)&vec));
+  double *r = vec, *z = r + nrhs * len, *p = z + nrhs * len, *Ap = p + nrhs * len;
+  char* sbuf = nullptr;
+  GS_TRY(ctx->scratch_buf(kSlotPcgScalars, sizeof(PcgScalars) + kRedBlocks * kMaxRhs * sizeof(double) + 256,
+                          (void**)&sbuf));
+  PcgScalars* s = (PcgScalars*)sbuf;
+  double* partials = (double*)(sbuf + ((sizeof(PcgScalars) + 255) / 256) * 256);
+  double *rl, *zl;
+  GS_TRY(mas_level_vectors(ctx, mas, nrhs, &rl, &zl));
+  GS_CUDA(cudaMemsetAsync(s, 0, sizeof(PcgScalars), st));
+  if (variant == GS_SPMV_ROW) GS_TRY(ensure_lower(ctx, mat));  // built once per matrix
+
+  const double tol2 = tol * tol;
+  k_init<<<kRedBlocks, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials);
+  GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
+  k_dot<true><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit);
+  const int poll = 4;
+  int* h_conv = ctx->h_pinned + 64;
+  for (int it = 0; it < max_iter; ++it) {
+    GS_TRY(spmv_launch(ctx, mat, p, Ap, nrhs, variant));
+    k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp);
+    k_update_xr<<<kRedBlocks, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2);
+    if (it + 1 == max_iter) break;
+    GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
+    k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz);
+    k_update_p<<<kRedBlocks * 4, kRedThreads, 0, st>>>(p, z, len, nrhs, s);
+    if ((it + 1) % poll == 0) {
+      GS_CUDA(cudaMemcpyAsync(h_conv, &s->all_conv, 4, cudaMemcpyDeviceToHost, st));
+      GS_CUDA(cudaStreamSynchronize(st));
+      if (*h_conv) break;
+    }
+  }
+  GS_CUDA(cudaGetLastError());
+  PcgScalars hs;
+  GS_CUDA(cudaMemcpyAsync(&hs, s, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  bool all = true;
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[k] = hs.iters[k];
+    if (rel_res) rel_res[k] = hs.bnorm2[k] > 0 ? std::sqrt(hs.rr[k] / hs.bnorm2[k]) : 0.0;
+    all = all && hs.conv[k];
+  }
+  int flags = 0;
+  GS_TRY(ctx->take_flags(&flags));
+  if (hs.flags) return status_from_flags(hs.flags);
+  if (flags) return status_from_flags(flags);
+  if (!all) {
+    set_error("gs_pcg_solve: not converged in %d iterations", max_iter);
+    return GS_ERR_MAXITER;
+  }
+  return GS_OK;
+}

@@ -1,0 +1,245 @@
+// Symmetric block SpMV on the stored diagonal + upper blocks (Sec. 5.3).
+//
+// GS_SPMV_SRBK follows Alg. SRBK: one thread per stored block (rows sorted),
+// H x_j is reduced per row with the warp head-segmented reduction and
+// finished with one atomic per segment head; off-diagonal blocks add
+// H^T x_b to y_j atomically.  y is zeroed first.
+//
+// GS_SPMV_ROW gathers each row instead: y_r = sum_{c >= r} A_rc x_c +
+// sum_{c < r} A_cr^T x_c, the second sum reading the same stored blocks
+// through a per-row list of transposed references (4-byte indices, built
+// once per matrix).  Eight lanes share a row and reduce in a fixed order,
+// so results are bit-reproducible and need no atomics or zeroing.
+//
+// On GB300 both are bound by FP64 FMA throughput (18 FMA per stored block
+// per right-hand side against 80 bytes per block read once for all RHS).
+#include <cub/device/device_radix_sort.cuh>
+
+#include "common.cuh"
+#include "primitives.cuh"
+
+namespace gs {
+
+template <int kR>
+__global__ void __launch_bounds__(256) k_spmv_srbk(const int32_t* __restrict__ rid, const int32_t* __restrict__ cid,
+                                                   const double* __restrict__ au, int64_t nnzb, int64_t stride,
+                                                   int nrhs, const double* __restrict__ x, double* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  bool in = i < nnzb;
+  int32_t b = in ? rid[i] : -1;
+  int32_t bp = (in && i > 0) ? rid[i - 1] : -1;
+  int32_t j = in ? cid[i] : 0;
+  bool head = lane == 0 || bp != b || !in;
+  unsigned hm = __ballot_sync(kFull, head);
+  int send = segment_end(hm, lane);
+  double H[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) H[k] = in ? au[i * 9 + k] : 0.0;
+  for (int r0 = 0; r0 < nrhs; r0 += kR) {
+    double v[kR * 3];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      const int r = r0 + q;
+      double xj0 = 0, xj1 = 0, xj2 = 0;
+      if (in && r < nrhs) {
+        const double* xr = x + r * stride;
+        xj0 = xr[3 * j], xj1 = xr[3 * j + 1], xj2 = xr[3 * j + 2];
+        if (b != j) {
+          double xb0 = xr[3 * b], xb1 = xr[3 * b + 1], xb2 = xr[3 * b + 2];
+          double* yr = y + r * stride + 3 * j;
+          atomicAdd(yr + 0, H[0] * xb0 + H[3] * xb1 + H[6] * xb2);
+          atomicAdd(yr + 1, H[1] * xb0 + H[4] * xb1 + H[7] * xb2);
+          atomicAdd(yr + 2, H[2] * xb0 + H[5] * xb1 + H[8] * xb2);
+        }
+      }
+      v[3 * q + 0] = H[0] * xj0 + H[1] * xj1 + H[2] * xj2;
+      v[3 * q + 1] = H[3] * xj0 + H[4] * xj1 + H[5] * xj2;
+      v[3 * q + 2] = H[6] * xj0 + H[7] * xj1 + H[8] * xj2;
+    }
+    head_segmented_reduce<kR * 3>(v, lane, send);
+    if (head && in) {
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        if (r0 + q < nrhs) {
+          double* yr = y + (r0 + q) * stride + 3 * b;
+          atomicAdd(yr + 0, v[3 * q + 0]);
+          atomicAdd(yr + 1, v[3 * q + 1]);
+          atomicAdd(yr + 2, v[3 * q + 2]);
+        }
+      }
+    }
+  }
+}
+
+// Eight lanes per block row; each lane strides over the row's entries
+// (its upper blocks first, then its transposed references).
+constexpr int kRowLanes = 8;
+
+template <int kR>
+__global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
+                                                  const int32_t* __restrict__ lo_ptr,
+                                                  const int32_t* __restrict__ lo_idx,
+                                                  const int32_t* __restrict__ lo_col, const double* __restrict__ au,
+                                                  int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
+                                                  double* __restrict__ y) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t row = (int32_t)(t / kRowLanes);
+  int sub = threadIdx.x % kRowLanes;
+  bool in = row < n;
+  int32_t u0 = 0, u1 = 0, l0 = 0, l1 = 0;
+  if (in) {
+    u0 = row_ptr[row], u1 = row_ptr[row + 1];
+    l0 = lo_ptr[row], l1 = lo_ptr[row + 1];
+  }
+  const int32_t nu = u1 - u0, total = nu + (l1 - l0);
+  for (int r0 = 0; r0 < nrhs; r0 += kR) {
+    double acc[kR * 3];
+#pragma unroll
+    for (int k = 0; k < kR * 3; ++k) acc[k] = 0.0;
+    for (int32_t e = sub; e < total; e += kRowLanes) {
+      bool upper = e < nu;
+      int64_t blk;
+      int32_t col;
+      if (upper) {
+        blk = u0 + e;
+        col = cid[blk];
+      } else {
+        blk = lo_idx[l0 + e - nu];
+        col = lo_col[l0 + e - nu];
+      }
+      double H[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) H[k] = au[blk * 9 + k];
+      if (!upper) {  // use the transpose
+        double t1 = H[1], t2 = H[2], t5 = H[5];
+        H[1] = H[3], H[2] = H[6], H[5] = H[7];
+        H[3] = t1, H[6] = t2, H[7] = t5;
+      }
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        if (r0 + q < nrhs) {
+          const double* xr = x + (r0 + q) * stride + 3 * col;
+          double x0 = xr[0], x1 = xr[1], x2 = xr[2];
+          acc[3 * q + 0] += H[0] * x0 + H[1] * x1 + H[2] * x2;
+          acc[3 * q + 1] += H[3] * x0 + H[4] * x1 + H[5] * x2;
+          acc[3 * q + 2] += H[6] * x0 + H[7] * x1 + H[8] * x2;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kR * 3; ++k) {
+#pragma unroll
+      for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o, kRowLanes);
+    }
+    if (in && sub == 0) {
+#pragma unroll
+      for (int q = 0; q < kR; ++q)
+        if (r0 + q < nrhs) {
+          double* yr = y + (r0 + q) * stride + 3 * row;
+          yr[0] = acc[3 * q + 0], yr[1] = acc[3 * q + 1], yr[2] = acc[3 * q + 2];
+        }
+    }
+  }
+}
+
+__global__ void k_lower_keys(const int32_t* __restrict__ rid, const int32_t* __restrict__ cid, int64_t nnzb,
+                             uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnzb) return;
+  bool off = rid[i] != cid[i];
+  key[i] = off ? (uint32_t)cid[i] : 0xffffffffu;  // transposed entry lands in row cid
+  val[i] = (uint32_t)i;
+}
+
+__global__ void k_lower_fill(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
+                             const int32_t* __restrict__ rid, int64_t m, int32_t n, int32_t* __restrict__ lo_ptr,
+                             int32_t* __restrict__ lo_idx, int32_t* __restrict__ lo_col) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > m) return;
+  int32_t r_here = (e < m) ? (int32_t)skey[e] : n;
+  int32_t r_prev = (e > 0) ? (int32_t)skey[e - 1] : -1;
+  for (int32_t r = r_prev + 1; r <= r_here; ++r) lo_ptr[r] = (int32_t)e;
+  if (e < m) {
+    lo_idx[e] = (int32_t)sval[e];
+    lo_col[e] = rid[sval[e]];
+  }
+}
+
+// Number of valid (non-sentinel) keys in a sorted key array.
+__global__ void k_count_valid(const uint32_t* __restrict__ k, int64_t nz, int32_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nz) return;
+  bool v = k[i] != 0xffffffffu;
+  bool vn = (i + 1 < nz) && (k[i + 1] != 0xffffffffu);
+  if (v && !vn) *out = (int32_t)(i + 1);
+}
+
+// Build the per-row transposed references once (the radix sort is stable,
+// so each row's references stay in ascending source row).
+int ensure_lower(gs_ctx ctx, gs_mat m) {
+  if (m->lo_ptr) return GS_OK;
+  cudaStream_t st = ctx->stream;
+  const int64_t nz = m->nnzb;
+  const int64_t cap = std::max<int64_t>(nz, 1);
+  uint32_t *k_in, *k_out, *v_in, *v_out;
+  int32_t* d_cnt;
+  GS_TRY(ctx->scratch_buf(kSlotSortKeysIn, cap * 4, (void**)&k_in));
+  GS_TRY(ctx->scratch_buf(kSlotSortKeysOut, cap * 4, (void**)&k_out));
+  GS_TRY(ctx->scratch_buf(kSlotSortValsIn, cap * 4, (void**)&v_in));
+  GS_TRY(ctx->scratch_buf(kSlotSortValsOut, cap * 4, (void**)&v_out));
+  GS_TRY(ctx->scratch_buf(kSlotReduce, 64, (void**)&d_cnt));
+  GS_CUDA(cudaMemsetAsync(d_cnt, 0, 4, st));
+  if (nz > 0) {
+    k_lower_keys<<<ceil_div(nz, 256), 256, 0, st>>>(m->rid, m->cid, nz, k_in, v_in);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, v_in, v_out, (int64_t)nz, 0, 32, st);
+    void* temp;
+    GS_TRY(ctx->scratch_buf(kSlotSortTemp, tb, &temp));
+    GS_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, v_in, v_out, (int64_t)nz, 0, 32, st));
+    k_count_valid<<<ceil_div(nz, 256), 256, 0, st>>>(k_out, nz, d_cnt);
+  }
+  GS_CUDA(cudaMemcpyAsync(ctx->h_pinned, d_cnt, 4, cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  const int64_t n_off = ctx->h_pinned[0];
+  GS_TRY(ctx->alloc((void**)&m->lo_ptr, (size_t)(m->n + 1) * 4));
+  GS_TRY(ctx->alloc((void**)&m->lo_idx, (size_t)std::max<int64_t>(n_off, 1) * 4));
+  GS_TRY(ctx->alloc((void**)&m->lo_col, (size_t)std::max<int64_t>(n_off, 1) * 4));
+  k_lower_fill<<<ceil_div(n_off + 1, 256), 256, 0, st>>>(k_out, v_out, m->rid, n_off, m->n, m->lo_ptr, m->lo_idx,
+                                                         m->lo_col);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+// y = A x on the context stream (no validation; used inside PCG).
+int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant) {
+  cudaStream_t st = ctx->stream;
+  const int64_t stride = 3LL * m->n;
+  if (variant == GS_SPMV_SRBK) {
+    GS_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * stride * sizeof(double), st));
+    if (m->nnzb > 0)
+      k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y);
+  } else {
+    GS_TRY(ensure_lower(ctx, m));
+    const int64_t threads = (int64_t)m->n * kRowLanes;
+    if (nrhs == 1)
+      k_spmv_row<1><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
+                                                            m->au, m->n, stride, nrhs, x, y);
+    else
+      k_spmv_row<4><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
+                                                            m->au, m->n, stride, nrhs, x, y);
+  }
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" int gs_spmv(gs_ctx ctx, gs_mat m, const double* x, double* y, int32_t nrhs, int32_t variant) {
+  GS_CHECK(ctx && m, GS_ERR_INVALID, "gs_spmv: null context or matrix");
+  GS_CHECK(nrhs >= 1, GS_ERR_INVALID, "gs_spmv: nrhs %d", nrhs);
+  GS_CHECK(x && y && x != y, GS_ERR_INVALID, "gs_spmv: null or aliased vectors");
+  GS_CHECK(variant == GS_SPMV_SRBK || variant == GS_SPMV_ROW, GS_ERR_INVALID, "gs_spmv: variant %d", variant);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  return gs::spmv_launch(ctx, m, x, y, nrhs, variant);
+}
