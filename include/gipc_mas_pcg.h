@@ -186,6 +186,31 @@ int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nr
                  int32_t max_iter, int32_t spmv_variant, double* x, int32_t* iters,
                  double* rel_res);
 
+/* ---------------------------------------------------------------- measurement */
+/* Kernel classes the library counts (and optionally times) per context.
+ * The split follows the paper's cost model T = T_ga + T_pa + N_pcg T_pcg
+ * with T_pcg = T_spmv + T_ap + T_dot + T_axpby (supplement Eq. 1-2). */
+#define GS_K_ASSEMBLE 0         /* key encode, run flags, segment reduction, row pointers */
+#define GS_K_LIBPRIM 1          /* radix sort / scan primitives from the CUDA toolkit (CUB) */
+#define GS_K_SPMV 2             /* symmetric SpMV */
+#define GS_K_MAS_LEVELS 3       /* connectivity masks, expansion, numbering, coarse tables */
+#define GS_K_MAS_MATRICES 4     /* level-matrix scatter and per-domain reduction */
+#define GS_K_MAS_INVERT 5       /* per-domain Cholesky inverses */
+#define GS_K_MAS_APPLY_L0 6     /* level-0 dense products fused with the prolongation */
+#define GS_K_MAS_APPLY_COARSE 7 /* restriction and coarse-level dense products */
+#define GS_K_PCG_VECTOR 8       /* dot products and vector updates */
+#define GS_K_OTHER 9            /* validation and setup kernels */
+#define GS_K_COUNT 10
+
+/* Start counting kernel launches per class on `ctx`; classes whose bit is
+ * set in `timed_classes` are also bracketed by CUDA events on the context
+ * stream (adds two event records per such launch). */
+int gs_profile_begin(gs_ctx ctx, uint32_t timed_classes);
+/* Stop, synchronise the stream and report per class: launches (host
+ * int64[GS_K_COUNT]) and summed event time in ms (host double[GS_K_COUNT],
+ * 0 for untimed classes).  Either output may be NULL. */
+int gs_profile_end(gs_ctx ctx, int64_t* launches, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

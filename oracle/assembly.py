@@ -33,9 +33,10 @@ def assemble(rows, cols, blocks):
     keep = rows <= cols
     keys = hash_key(rows[keep], cols[keep])
     uk, inv = np.unique(keys, return_inverse=True)
-    R = np.zeros((uk.size, 3, 3))
-    np.add.at(R, inv, blocks[keep])
-    return (uk >> 32).astype(np.int32), (uk & 0xFFFFFFFF).astype(np.int32), R
+    kept = blocks[keep].reshape(-1, 9)
+    # per entry: the sum, in input order, of the values sharing a key
+    R = np.stack([np.bincount(inv, weights=kept[:, e], minlength=uk.size) for e in range(9)], -1)
+    return (uk >> 32).astype(np.int32), (uk & 0xFFFFFFFF).astype(np.int32), R.reshape(-1, 3, 3)
 
 
 def assemble_dict(rows, cols, blocks):

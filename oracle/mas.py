@@ -39,6 +39,7 @@ Test infrastructure only (see the package docstring).
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.sparse as sp
 
 
 class NotSPDError(ValueError):
@@ -182,7 +183,16 @@ def invert_domains(lv, mats):
     return invs
 
 
-def apply(lv, invs, r):
+def coarsener(lv, l):
+    """C_l of supplement Eq. 5-6 as a sparse 0/1 matrix acting on nodes:
+    row a (an item of level l, padded domains included) sums the nodes u with
+    coarse[l][u] = a.  Applied to (V, m) arrays it acts on each 3-vector."""
+    V = lv.coarse[0].size
+    n_pad = lv.n_domains(l) * lv.N
+    return sp.csr_matrix((np.ones(V), (lv.coarse[l], np.arange(V))), shape=(n_pad, V))
+
+
+def apply(lv, invs, r, C=None):
     """z = sum_l C_l^T M_l^{-1} C_l r for r of shape (..., V, 3) or (..., 3V)."""
     N = lv.N
     r = np.asarray(r, dtype=np.float64)
@@ -191,13 +201,16 @@ def apply(lv, invs, r):
     r3 = r.reshape(shape[:-1] + (V, 3)) if shape[-1] == 3 * V else r
     lead = r3.shape[:-2]
     r3 = r3.reshape((-1, V, 3))
-    z = np.zeros_like(r3)
+    K = r3.shape[0]
+    R = r3.transpose(1, 0, 2).reshape(V, 3 * K)  # node-major
+    Z = np.zeros_like(R)
     for l in range(lv.n_levels):
+        Cl = C[l] if C is not None else coarsener(lv, l)
         nd = lv.n_domains(l)
-        rl = np.zeros((r3.shape[0], nd * N, 3))
-        np.add.at(rl, (slice(None), lv.coarse[l]), r3)
-        zl = np.einsum("dij,kdj->kdi", invs[l], rl.reshape(r3.shape[0], nd, 3 * N))
-        z += zl.reshape(r3.shape[0], nd * N, 3)[:, lv.coarse[l]]
+        rl = (Cl @ R).reshape(nd, N, K, 3).transpose(0, 1, 3, 2).reshape(nd, 3 * N, K)
+        zl = np.matmul(invs[l], rl)  # block-diagonal M_l^{-1}, one dense product per domain
+        Z += Cl.T @ zl.reshape(nd, N, 3, K).transpose(0, 1, 3, 2).reshape(nd * N, 3 * K)
+    z = Z.reshape(V, K, 3).transpose(1, 0, 2)
     return z.reshape(lead + (V, 3)).reshape(shape)
 
 
@@ -206,9 +219,14 @@ class MAS:
     levels: Levels
     mats: list
     invs: list
+    C: list = field(default_factory=list)
+
+    def __post_init__(self):
+        if not self.C:
+            self.C = [coarsener(self.levels, l) for l in range(self.levels.n_levels)]
 
     def __call__(self, r):
-        return apply(self.levels, self.invs, r)
+        return apply(self.levels, self.invs, r, self.C)
 
 
 def build_mas(map_, N, max_levels, adj_ptr, adj, contacts, rid, cid, au):

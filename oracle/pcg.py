@@ -15,6 +15,32 @@ Test infrastructure only (see the package docstring).
 """
 
 import numpy as np
+import scipy.sparse as sp
+
+
+class SymmetricMatrix:
+    """The full symmetric matrix of the stored diagonal + upper blocks (Sec. 5.3).
+
+    Block (r, c) of the stored list and, off the diagonal, its transpose at
+    (c, r) are laid out as a scipy block-sparse (BSR) matrix; ``A @ x`` is
+    then the library's sparse product.  x: (3n,) or (3n, k).
+    """
+
+    def __init__(self, n, rid, cid, au):
+        rid = np.asarray(rid, dtype=np.int64)
+        cid = np.asarray(cid, dtype=np.int64)
+        au = np.asarray(au, dtype=np.float64).reshape(-1, 3, 3)
+        off = rid != cid
+        r = np.concatenate([rid, cid[off]])
+        c = np.concatenate([cid, rid[off]])
+        d = np.concatenate([au, np.swapaxes(au[off], 1, 2)])
+        order = np.lexsort((c, r))
+        indptr = np.concatenate([[0], np.cumsum(np.bincount(r, minlength=n))])
+        self.n = n
+        self.A = sp.bsr_matrix((d[order], c[order], indptr), shape=(3 * n, 3 * n), blocksize=(3, 3))
+
+    def __call__(self, x):
+        return self.A @ x
 
 
 def spmv(rid, cid, au, x):

@@ -27,6 +27,21 @@ GS_SPMV_ROW = 1
 GS_PREC_FP64 = 0
 GS_PREC_FP32 = 1
 
+# kernel classes of the profiler (supplement Eq. 1-2 cost split)
+GS_K_ASSEMBLE = 0
+GS_K_LIBPRIM = 1
+GS_K_SPMV = 2
+GS_K_MAS_LEVELS = 3
+GS_K_MAS_MATRICES = 4
+GS_K_MAS_INVERT = 5
+GS_K_MAS_APPLY_L0 = 6
+GS_K_MAS_APPLY_COARSE = 7
+GS_K_PCG_VECTOR = 8
+GS_K_OTHER = 9
+GS_K_COUNT = 10
+K_NAMES = ["assemble", "libprim", "spmv", "mas_levels", "mas_matrices", "mas_invert", "mas_apply_l0",
+           "mas_apply_coarse", "pcg_vector", "other"]
+
 # Every symbol the header declares (checked by the test-suite).
 EXPORTS = [
     "gs_status_string",
@@ -48,6 +63,8 @@ EXPORTS = [
     "gs_mas_apply",
     "gs_mas_destroy",
     "gs_pcg_solve",
+    "gs_profile_begin",
+    "gs_profile_end",
 ]
 
 
@@ -104,6 +121,8 @@ def lib():
             "gs_mas_apply": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
             "gs_mas_destroy": (ctypes.c_int, [_P]),
             "gs_pcg_solve": (ctypes.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _I32, _P, _P, _P]),
+            "gs_profile_begin": (ctypes.c_int, [_P, ctypes.c_uint32]),
+            "gs_profile_end": (ctypes.c_int, [_P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -291,3 +310,19 @@ def gs_pcg_solve(ctx, mat, mas, b, x, nrhs=1, tol=1e-6, max_iter=10_000, variant
     if s != GS_OK and not (s == GS_ERR_MAXITER and not raise_on_maxiter):
         raise GsError(s, "gs_pcg_solve")
     return iters, rel, s
+
+
+# ----------------------------------------------------------------- measurement
+def gs_profile_begin(ctx, timed_classes=()):
+    mask = 0
+    for k in timed_classes:
+        mask |= 1 << k
+    _check(lib().gs_profile_begin(ctx, mask), "gs_profile_begin")
+
+
+def gs_profile_end(ctx):
+    """Returns (launches int64[GS_K_COUNT], ms float64[GS_K_COUNT])."""
+    launches = np.zeros(GS_K_COUNT, dtype=np.int64)
+    ms = np.zeros(GS_K_COUNT, dtype=np.float64)
+    _check(lib().gs_profile_end(ctx, launches.ctypes.data_as(_P), ms.ctypes.data_as(_P)), "gs_profile_end")
+    return launches, ms

@@ -114,7 +114,7 @@ extern "C" int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32
   GS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   AbdMap m{body_of_node, xbar, n_fem, n_bodies};
-  k_abd_validate<<<ceil_div(n_nodes, 256), 256, 0, st>>>(m, n_nodes, ctx->d_flags);
+  { GS_PROF(ctx, GS_K_OTHER); k_abd_validate<<<ceil_div(n_nodes, 256), 256, 0, st>>>(m, n_nodes, ctx->d_flags); }
   int flags = 0;
   GS_TRY(ctx->take_flags(&flags));
   if (flags) return status_from_flags(flags);
@@ -130,13 +130,13 @@ extern "C" int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32
   if ((s = ctx->alloc((void**)&cnt, (size_t)(U + 1) * 4)) || (s = ctx->alloc((void**)&off, (size_t)(U + 1) * 4)))
     goto done;
   if (U > 0) {
-    k_abd_expand<0><<<ceil_div(U, 256), 256, 0, st>>>(m, lvl1->rid, lvl1->cid, lvl1->au, U, nullptr, cnt, nullptr,
-                                                      nullptr, nullptr);
+    { GS_PROF(ctx, GS_K_ASSEMBLE); k_abd_expand<0><<<ceil_div(U, 256), 256, 0, st>>>(m, lvl1->rid, lvl1->cid, lvl1->au, U, nullptr, cnt, nullptr,
+                                                      nullptr, nullptr); }
   }
   cudaMemsetAsync(cnt + U, 0, 4, st);
   cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, off, (int64_t)(U + 1), st);
   if ((s = ctx->alloc(&temp, tb))) goto done;
-  cub::DeviceScan::ExclusiveSum(temp, tb, cnt, off, (int64_t)(U + 1), st);
+  { GS_PROF(ctx, GS_K_LIBPRIM); cub::DeviceScan::ExclusiveSum(temp, tb, cnt, off, (int64_t)(U + 1), st); }
   if (cudaMemcpyAsync(ctx->h_pinned, off + U, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("gs_assemble_abd: readback failed");
@@ -148,8 +148,8 @@ extern "C" int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32
       (s = ctx->alloc((void**)&oblk, (size_t)total * 72)))
     goto done;
   if (U > 0) {
-    k_abd_expand<1><<<ceil_div(U, 256), 256, 0, st>>>(m, lvl1->rid, lvl1->cid, lvl1->au, U, off, nullptr, orow,
-                                                      ocol, oblk);
+    { GS_PROF(ctx, GS_K_ASSEMBLE); k_abd_expand<1><<<ceil_div(U, 256), 256, 0, st>>>(m, lvl1->rid, lvl1->cid, lvl1->au, U, off, nullptr, orow,
+                                                      ocol, oblk); }
   }
   s = gs_assemble(ctx, (int32_t)n_red, orow, ocol, oblk, total, out);
 done:

@@ -132,21 +132,25 @@ int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* col
       return fail(s);
     O = P + nb;
     const int T = 256;
-    k_encode_keys<<<ceil_div(nb, T), T, 0, st>>>(rows, cols, nb, n, shift, sentinel, k_in, i_in, ctx->d_flags);
+    { GS_PROF(ctx, GS_K_ASSEMBLE); k_encode_keys<<<ceil_div(nb, T), T, 0, st>>>(rows, cols, nb, n, shift, sentinel, k_in, i_in, ctx->d_flags); }
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0, end_bit, st);
     void* temp = nullptr;
     if ((s = ctx->scratch_buf(kSlotSortTemp, tb, &temp))) return fail(s);
-    if (cudaSuccess != cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0,
-                                                       end_bit, st)) {
+    cudaError_t se;
+    {
+      GS_PROF(ctx, GS_K_LIBPRIM);
+      se = cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0, end_bit, st);
+    }
+    if (se != cudaSuccess) {
       set_error("radix sort failed");
       return fail(GS_ERR_CUDA);
     }
-    k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(k_out, nb, P);
+    { GS_PROF(ctx, GS_K_ASSEMBLE); k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(k_out, nb, P); }
     size_t sb = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, sb, P, O, (int64_t)nb, st);
     if ((s = ctx->scratch_buf(kSlotSortTemp, std::max(sb, tb), &temp))) return fail(s);
-    cub::DeviceScan::ExclusiveSum(temp, sb, P, O, (int64_t)nb, st);
+    { GS_PROF(ctx, GS_K_LIBPRIM); cub::DeviceScan::ExclusiveSum(temp, sb, P, O, (int64_t)nb, st); }
     // U = distinct keys, minus the sentinel group if present.
     uint64_t* hk = (uint64_t*)ctx->h_pinned;
     int32_t* ho = (int32_t*)(ctx->h_pinned + 4);
@@ -170,10 +174,10 @@ int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* col
   if (U > 0) {
     if (cudaMemsetAsync(m->au, 0, (size_t)U * 9 * sizeof(double), st) != cudaSuccess) return fail(GS_ERR_CUDA);
     const int T = 256;
-    k_fast_segment_reduce<<<ceil_div(nb, T), T, 0, st>>>(k_out, i_out, O, blocks, nb, sentinel, shift, m->au,
-                                                            m->rid, m->cid);
+    { GS_PROF(ctx, GS_K_ASSEMBLE); k_fast_segment_reduce<<<ceil_div(nb, T), T, 0, st>>>(k_out, i_out, O, blocks, nb, sentinel, shift, m->au,
+                                                            m->rid, m->cid); }
   }
-  k_row_ptr<<<ceil_div(U + 1, 256), 256, 0, st>>>(m->rid, U, n, m->row_ptr);
+  { GS_PROF(ctx, GS_K_ASSEMBLE); k_row_ptr<<<ceil_div(U + 1, 256), 256, 0, st>>>(m->rid, U, n, m->row_ptr); }
   if (cudaGetLastError() != cudaSuccess) {
     set_error("assembly kernel launch failed");
     return fail(GS_ERR_CUDA);

@@ -58,7 +58,24 @@ struct Buffer {
 
 }  // namespace gs
 
+namespace gs {
+// Per-context launch counters and optional CUDA-event timing per class.
+struct Prof {
+  bool on = false;
+  uint32_t timed = 0;
+  int64_t launches[GS_K_COUNT] = {};
+  double ms[GS_K_COUNT] = {};
+  struct Pending {
+    int klass;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+}  // namespace gs
+
 struct gs_ctx_s {
+  gs::Prof prof;
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
@@ -96,6 +113,16 @@ enum ScratchSlot : int {
   kSlotMasBuild3,
   kSlotCount
 };
+
+// Counts (and, if requested, times) the launch made inside its scope.
+struct ProfScope {
+  gs_ctx ctx;
+  int klass;
+  cudaEvent_t a = nullptr;
+  ProfScope(gs_ctx c, int k);
+  ~ProfScope();
+};
+#define GS_PROF(ctx, klass) ::gs::ProfScope gs_prof_scope_((ctx), (klass))
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

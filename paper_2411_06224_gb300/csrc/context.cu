@@ -30,6 +30,35 @@ int status_from_flags(int flags) {
   return GS_OK;
 }
 
+static cudaEvent_t take_event(Prof& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(gs_ctx c, int k) : ctx(c), klass(k) {
+  Prof& p = ctx->prof;
+  if (!p.on) return;
+  p.launches[k] += 1;
+  if (p.timed & (1u << k)) {
+    a = take_event(p);
+    cudaEventRecord(a, ctx->stream);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  Prof& p = ctx->prof;
+  cudaEvent_t b = take_event(p);
+  cudaEventRecord(b, ctx->stream);
+  p.pending.push_back({klass, a, b});
+}
+
 }  // namespace gs
 
 int gs_ctx_s::alloc(void** p, size_t bytes) {
@@ -124,6 +153,37 @@ int gs_create(gs_ctx* out, int device, void* stream) {
   return GS_OK;
 }
 
+int gs_profile_begin(gs_ctx ctx, uint32_t timed_classes) {
+  GS_CHECK(ctx, GS_ERR_INVALID, "gs_profile_begin: null context");
+  gs::Prof& p = ctx->prof;
+  for (auto& q : p.pending) p.pool.push_back(q.a), p.pool.push_back(q.b);
+  p.pending.clear();
+  for (int k = 0; k < GS_K_COUNT; ++k) p.launches[k] = 0, p.ms[k] = 0.0;
+  p.timed = timed_classes;
+  p.on = true;
+  return GS_OK;
+}
+
+int gs_profile_end(gs_ctx ctx, int64_t* launches, double* ms) {
+  GS_CHECK(ctx, GS_ERR_INVALID, "gs_profile_end: null context");
+  gs::Prof& p = ctx->prof;
+  GS_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& q : p.pending) {
+    float t = 0.f;
+    GS_CUDA(cudaEventElapsedTime(&t, q.a, q.b));
+    p.ms[q.klass] += t;
+    p.pool.push_back(q.a);
+    p.pool.push_back(q.b);
+  }
+  p.pending.clear();
+  p.on = false;
+  for (int k = 0; k < GS_K_COUNT; ++k) {
+    if (launches) launches[k] = p.launches[k];
+    if (ms) ms[k] = p.ms[k];
+  }
+  return GS_OK;
+}
+
 int gs_set_stream(gs_ctx ctx, void* stream) {
   GS_CHECK(ctx != nullptr, GS_ERR_INVALID, "gs_set_stream: null context");
   ctx->stream = (cudaStream_t)stream;
@@ -133,6 +193,8 @@ int gs_set_stream(gs_ctx ctx, void* stream) {
 int gs_destroy(gs_ctx ctx) {
   if (!ctx) return GS_OK;
   cudaSetDevice(ctx->device);
+  for (auto& q : ctx->prof.pending) ctx->prof.pool.push_back(q.a), ctx->prof.pool.push_back(q.b);
+  for (auto e : ctx->prof.pool) cudaEventDestroy(e);
   for (auto& b : ctx->scratch) ctx->release(b.ptr);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_flags);

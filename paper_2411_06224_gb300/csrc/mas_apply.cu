@@ -138,13 +138,13 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const in
   GS_CHECK(threads <= 1024, GS_ERR_UNSUPPORTED, "mas apply: too many right-hand sides (%d)", nrhs);
   if (mas->L > 1) {
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
-    k_restrict<<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(r, stride, nrhs, mas->remap0,
-                                                                              mas->n_domains[0], al, rl, lstride);
-    k_domain_product<Tm, kRPT, 0><<<n_coarse_jobs, threads, smem, st>>>(
-        d_inv, d_jobs, d_jobs + n_coarse_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al);
+    { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(r, stride, nrhs, mas->remap0,
+                                                                              mas->n_domains[0], al, rl, lstride); }
+    { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_domain_product<Tm, kRPT, 0><<<n_coarse_jobs, threads, smem, st>>>(
+        d_inv, d_jobs, d_jobs + n_coarse_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al); }
   }
-  k_domain_product<Tm, kRPT, 1><<<mas->n_domains[0], threads, smem, st>>>(d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride,
-                                                                         mas->remap0, rl, zl, lstride, al);
+  { GS_PROF(ctx, GS_K_MAS_APPLY_L0); k_domain_product<Tm, kRPT, 1><<<mas->n_domains[0], threads, smem, st>>>(d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride,
+                                                                         mas->remap0, rl, zl, lstride, al); }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

@@ -410,8 +410,8 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   // remap + validation of map
   if ((s = ctx->alloc((void**)&mas->remap0, (size_t)n_slots * 4))) return fail(s);
   if (cudaMemsetAsync(mas->remap0, 0xff, (size_t)n_slots * 4, st) != cudaSuccess) return fail(GS_ERR_CUDA);
-  k_build_remap<<<ceil_div(n, 256), 256, 0, st>>>(map, n, n_slots, mas->remap0, ctx->d_flags);
-  k_csr_ptr_check<<<ceil_div(n, 256), 256, 0, st>>>(adj_ptr, n, ctx->d_flags);
+  { GS_PROF(ctx, GS_K_OTHER); k_build_remap<<<ceil_div(n, 256), 256, 0, st>>>(map, n, n_slots, mas->remap0, ctx->d_flags); }
+  { GS_PROF(ctx, GS_K_OTHER); k_csr_ptr_check<<<ceil_div(n, 256), 256, 0, st>>>(adj_ptr, n, ctx->d_flags); }
   int flags = 0;
   if ((s = ctx->take_flags(&flags))) return fail(s);
   if (flags) return fail(status_from_flags(flags));
@@ -425,10 +425,10 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   int32_t *src = nullptr, *dst = nullptr;
   if ((s = ctx->scratch_buf(kSlotMasBuild0, (size_t)std::max<int64_t>(E, 1) * 8, (void**)&src))) return fail(s);
   dst = src + std::max<int64_t>(E, 1);
-  k_edges_from_csr<<<ceil_div(n, 256), 256, 0, st>>>(adj_ptr, adj, n, src, dst, ctx->d_flags);
+  { GS_PROF(ctx, GS_K_MAS_LEVELS); k_edges_from_csr<<<ceil_div(n, 256), 256, 0, st>>>(adj_ptr, adj, n, src, dst, ctx->d_flags); }
   if (n_contacts > 0)
-    k_edges_from_contacts<<<ceil_div(n_contacts, 256), 256, 0, st>>>(contacts, n_contacts, n, nnz_adj, src, dst,
-                                                                     ctx->d_flags);
+    { GS_PROF(ctx, GS_K_MAS_LEVELS); k_edges_from_contacts<<<ceil_div(n_contacts, 256), 256, 0, st>>>(contacts, n_contacts, n, nnz_adj, src, dst,
+                                                                     ctx->d_flags); }
   if ((s = ctx->take_flags(&flags))) return fail(s);
   if (flags) return fail(status_from_flags(flags));
 
@@ -454,15 +454,15 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     if (items <= N) break;
     const int32_t* cl = mas->coarse[l];
     if (cudaMemsetAsync(mask, 0, (size_t)ndom * N * 4, st) != cudaSuccess) return fail(GS_ERR_CUDA);
-    k_mask_init<<<ceil_div(n, 256), 256, 0, st>>>(cl, n, N, mask);
-    if (E > 0) k_edge_masks<<<ceil_div(E, 256), 256, 0, st>>>(src, dst, E, cl, N, mask);
-    k_expand_number<<<ceil_div((int64_t)ndom * 32, 256), 256, 0, st>>>(mask, ndom, N, local_id, count);
+    { GS_PROF(ctx, GS_K_MAS_LEVELS); k_mask_init<<<ceil_div(n, 256), 256, 0, st>>>(cl, n, N, mask); }
+    if (E > 0) { GS_PROF(ctx, GS_K_MAS_LEVELS); k_edge_masks<<<ceil_div(E, 256), 256, 0, st>>>(src, dst, E, cl, N, mask); }
+    { GS_PROF(ctx, GS_K_MAS_LEVELS); k_expand_number<<<ceil_div((int64_t)ndom * 32, 256), 256, 0, st>>>(mask, ndom, N, local_id, count); }
     cudaMemsetAsync(count + ndom, 0, 4, st);
     size_t tb = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, tb, count, dom_off, ndom + 1, st);
     void* temp;
     if ((s = ctx->scratch_buf(kSlotSortTemp, tb, &temp))) return fail(s);
-    cub::DeviceScan::ExclusiveSum(temp, tb, count, dom_off, ndom + 1, st);
+    { GS_PROF(ctx, GS_K_LIBPRIM); cub::DeviceScan::ExclusiveSum(temp, tb, count, dom_off, ndom + 1, st); }
     if (cudaMemcpyAsync(ctx->h_pinned, dom_off + ndom, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return fail(GS_ERR_CUDA);
@@ -471,7 +471,7 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     int32_t* cn = nullptr;
     if ((s = ctx->alloc((void**)&cn, (size_t)n * 4))) return fail(s);
     mas->coarse.push_back(cn);
-    k_next_of_node<<<ceil_div(n, 256), 256, 0, st>>>(cl, n, N, local_id, dom_off, cn);
+    { GS_PROF(ctx, GS_K_MAS_LEVELS); k_next_of_node<<<ceil_div(n, 256), 256, 0, st>>>(cl, n, N, local_id, dom_off, cn); }
     mas->n_items.push_back(n_next);
     mas->n_domains.push_back(ceil_div(n_next, N));
     n_real = n_next;
@@ -493,8 +493,8 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     lp.mat[l] = m;
   }
   if (mat->nnzb > 0)
-    k_scatter_blocks<<<ceil_div(mat->nnzb, 256), 256, 0, st>>>(mat->rid, mat->cid, mat->au, mat->nnzb, lp);
-  if (L > 1) k_domain_reduce<<<ceil_div((int64_t)n_dom0 * 32, 256), 256, 0, st>>>(mas->remap0, n_dom0, lp);
+    { GS_PROF(ctx, GS_K_MAS_MATRICES); k_scatter_blocks<<<ceil_div(mat->nnzb, 256), 256, 0, st>>>(mat->rid, mat->cid, mat->au, mat->nnzb, lp); }
+  if (L > 1) { GS_PROF(ctx, GS_K_MAS_MATRICES); k_domain_reduce<<<ceil_div((int64_t)n_dom0 * 32, 256), 256, 0, st>>>(mas->remap0, n_dom0, lp); }
   // inversion jobs: every domain of every level
   std::vector<int32_t> h_level, h_index;
   for (int l = 0; l < L; ++l)
@@ -515,15 +515,15 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   const size_t smem = (size_t)(3 * N) * (3 * N + 1) * sizeof(double);
   if (cudaFuncSetAttribute(k_invert_domains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return fail(GS_ERR_CUDA);
-  k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
-                                            ctx->d_flags);
+  { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
+                                            ctx->d_flags); }
   if (opts->precision == GS_PREC_FP32) {
     for (int l = 0; l < L; ++l) {
       float* f = nullptr;
       int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
       if ((s = ctx->alloc((void**)&f, (size_t)cnt * 4))) return fail(s);
       mas->inv32.push_back(f);
-      k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt);
+      { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt); }
     }
   }
   // multilevel vector layout for the apply (levels >= 1, padded per domain)

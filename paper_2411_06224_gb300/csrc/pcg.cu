@@ -217,19 +217,19 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   if (variant == GS_SPMV_ROW) GS_TRY(ensure_lower(ctx, mat));  // built once per matrix
 
   const double tol2 = tol * tol;
-  k_init<<<kRedBlocks, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials);
+  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_init<<<kRedBlocks, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials); }
   GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
-  k_dot<true><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit);
+  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<true><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit); }
   const int poll = 4;
   int* h_conv = ctx->h_pinned + 64;
   for (int it = 0; it < max_iter; ++it) {
     GS_TRY(spmv_launch(ctx, mat, p, Ap, nrhs, variant));
-    k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp);
-    k_update_xr<<<kRedBlocks, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2);
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_xr<<<kRedBlocks, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2); }
     if (it + 1 == max_iter) break;
     GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
-    k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz);
-    k_update_p<<<kRedBlocks * 4, kRedThreads, 0, st>>>(p, z, len, nrhs, s);
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_p<<<kRedBlocks * 4, kRedThreads, 0, st>>>(p, z, len, nrhs, s); }
     if ((it + 1) % poll == 0) {
       GS_CUDA(cudaMemcpyAsync(h_conv, &s->all_conv, 4, cudaMemcpyDeviceToHost, st));
       GS_CUDA(cudaStreamSynchronize(st));

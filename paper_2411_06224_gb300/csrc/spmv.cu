@@ -191,13 +191,13 @@ int ensure_lower(gs_ctx ctx, gs_mat m) {
   GS_TRY(ctx->scratch_buf(kSlotReduce, 64, (void**)&d_cnt));
   GS_CUDA(cudaMemsetAsync(d_cnt, 0, 4, st));
   if (nz > 0) {
-    k_lower_keys<<<ceil_div(nz, 256), 256, 0, st>>>(m->rid, m->cid, nz, k_in, v_in);
+    { GS_PROF(ctx, GS_K_OTHER); k_lower_keys<<<ceil_div(nz, 256), 256, 0, st>>>(m->rid, m->cid, nz, k_in, v_in); }
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, v_in, v_out, (int64_t)nz, 0, 32, st);
     void* temp;
     GS_TRY(ctx->scratch_buf(kSlotSortTemp, tb, &temp));
-    GS_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, v_in, v_out, (int64_t)nz, 0, 32, st));
-    k_count_valid<<<ceil_div(nz, 256), 256, 0, st>>>(k_out, nz, d_cnt);
+    { GS_PROF(ctx, GS_K_LIBPRIM); GS_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, v_in, v_out, (int64_t)nz, 0, 32, st)); }
+    { GS_PROF(ctx, GS_K_OTHER); k_count_valid<<<ceil_div(nz, 256), 256, 0, st>>>(k_out, nz, d_cnt); }
   }
   GS_CUDA(cudaMemcpyAsync(ctx->h_pinned, d_cnt, 4, cudaMemcpyDeviceToHost, st));
   GS_CUDA(cudaStreamSynchronize(st));
@@ -205,8 +205,8 @@ int ensure_lower(gs_ctx ctx, gs_mat m) {
   GS_TRY(ctx->alloc((void**)&m->lo_ptr, (size_t)(m->n + 1) * 4));
   GS_TRY(ctx->alloc((void**)&m->lo_idx, (size_t)std::max<int64_t>(n_off, 1) * 4));
   GS_TRY(ctx->alloc((void**)&m->lo_col, (size_t)std::max<int64_t>(n_off, 1) * 4));
-  k_lower_fill<<<ceil_div(n_off + 1, 256), 256, 0, st>>>(k_out, v_out, m->rid, n_off, m->n, m->lo_ptr, m->lo_idx,
-                                                         m->lo_col);
+  { GS_PROF(ctx, GS_K_OTHER); k_lower_fill<<<ceil_div(n_off + 1, 256), 256, 0, st>>>(k_out, v_out, m->rid, n_off, m->n, m->lo_ptr, m->lo_idx,
+                                                         m->lo_col); }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -218,16 +218,16 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
   if (variant == GS_SPMV_SRBK) {
     GS_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * stride * sizeof(double), st));
     if (m->nnzb > 0)
-      k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y);
+      { GS_PROF(ctx, GS_K_SPMV); k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y); }
   } else {
     GS_TRY(ensure_lower(ctx, m));
     const int64_t threads = (int64_t)m->n * kRowLanes;
     if (nrhs == 1)
-      k_spmv_row<1><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
-                                                            m->au, m->n, stride, nrhs, x, y);
+      { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
+                                                            m->au, m->n, stride, nrhs, x, y); }
     else
-      k_spmv_row<4><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
-                                                            m->au, m->n, stride, nrhs, x, y);
+      { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
+                                                            m->au, m->n, stride, nrhs, x, y); }
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
