@@ -79,6 +79,7 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
+  int spmv_cfg = 0;           // row-gather SpMV shape (tuning; env GS_SPMV_CFG)
   int* d_flags = nullptr;     // device error word
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
   std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls

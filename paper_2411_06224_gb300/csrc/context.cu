@@ -1,5 +1,6 @@
 // Context, errors and stream-ordered memory.
 #include <cstdarg>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -134,6 +135,7 @@ int gs_create(gs_ctx* out, int device, void* stream) {
     return GS_ERR_CUDA;
   }
   c->sm_count = prop.multiProcessorCount;
+  if (const char* cfg = getenv("GS_SPMV_CFG")) c->spmv_cfg = atoi(cfg);
   // Keep freed pool memory cached by the pool instead of returning it to
   // the driver at every synchronisation.
   cudaMemPool_t pool;

@@ -117,6 +117,31 @@ __global__ void __launch_bounds__(1024) k_domain_product(
   }
 }
 
+// Coarse levels hold few domains, so each output (row i of a domain, RHS k)
+// gets its own thread: the 3N-long dot product reads row i of the symmetric
+// inverse as column i (coalesced across i) and broadcasts r.
+template <typename Tm>
+__global__ void __launch_bounds__(256) k_coarse_product(const Tm* const* __restrict__ inv,
+                                                        const int32_t* __restrict__ job_level,
+                                                        const int32_t* __restrict__ job_dom, int n_jobs, int N,
+                                                        int nrhs, const double* __restrict__ rl,
+                                                        double* __restrict__ zl, int64_t lstride, ApplyLevels al) {
+  const int ld = 3 * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per_job = (int64_t)ld * nrhs;
+  if (t >= per_job * n_jobs) return;
+  const int job = (int)(t / per_job);
+  const int rem = (int)(t % per_job);
+  const int k = rem / ld, i = rem % ld;
+  const int l = job_level[job];
+  const int32_t d = job_dom[job];
+  const Tm* Mi = inv[l] + (int64_t)d * ld * ld;
+  const double* rj = rl + k * lstride + 3 * (al.vec_off[l] + (int64_t)d * N);
+  Tm acc = (Tm)0;
+  for (int j = 0; j < ld; ++j) acc += Mi[(int64_t)j * ld + i] * (Tm)rj[j];
+  zl[k * lstride + 3 * (al.vec_off[l] + (int64_t)d * N) + i] = (double)acc;
+}
+
 template <typename Tm>
 static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const int32_t* d_jobs, int n_coarse_jobs,
                         const double* r, double* z, int nrhs, double* rl, double* zl) {
@@ -140,8 +165,12 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const in
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
     { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(r, stride, nrhs, mas->remap0,
                                                                               mas->n_domains[0], al, rl, lstride); }
-    { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_domain_product<Tm, kRPT, 0><<<n_coarse_jobs, threads, smem, st>>>(
-        d_inv, d_jobs, d_jobs + n_coarse_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al); }
+    {
+      GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
+      const int64_t outs = (int64_t)n_coarse_jobs * ld * nrhs;
+      k_coarse_product<Tm><<<ceil_div(outs, 256), 256, 0, st>>>(d_inv, d_jobs, d_jobs + n_coarse_jobs, n_coarse_jobs,
+                                                                N, nrhs, rl, zl, lstride, al);
+    }
   }
   { GS_PROF(ctx, GS_K_MAS_APPLY_L0); k_domain_product<Tm, kRPT, 1><<<mas->n_domains[0], threads, smem, st>>>(d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride,
                                                                          mas->remap0, rl, zl, lstride, al); }

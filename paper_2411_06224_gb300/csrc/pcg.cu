@@ -14,6 +14,7 @@
 // A RHS stops moving once converged (alpha = 0), which keeps each RHS on
 // exactly its own single-RHS recurrence.  Kernels return at once after
 // every RHS converged; the host only polls that flag every few iterations.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -27,8 +28,8 @@ int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl
 int ensure_lower(gs_ctx ctx, gs_mat m);
 
 constexpr int kMaxRhs = 32;
-constexpr int kRedBlocks = 296;  // fixed grid of the reductions (2 per SM on 148+ SMs)
 constexpr int kRedThreads = 256;
+constexpr int kMaxRedBlocks = 256;  // reduction blocks per right-hand side
 
 struct PcgScalars {
   double bnorm2[kMaxRhs];
@@ -45,110 +46,136 @@ struct PcgScalars {
 
 enum DotOp : int { kOpBnorm = 0, kOpRzInit, kOpPAp, kOpRR, kOpRz };
 
-// Block-level sum of nrhs values per thread into partials[block][k].
-__device__ __forceinline__ void block_partials(double (&v)[kMaxRhs], int nrhs, double* __restrict__ partials) {
-  __shared__ double red[kRedThreads / 32][kMaxRhs];
+// Grid of the vector kernels: (G, nrhs); block (g, k) covers a contiguous
+// chunk of right-hand side k.  G depends only on the vector length, so the
+// reduction order -- and therefore the result -- is fixed.
+inline int red_blocks(int64_t len) {
+  int64_t g = (len + kRedThreads * 8 - 1) / (kRedThreads * 8);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kRedThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = 0; k < nrhs; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) red[w][k] = s;
+  v = warp_sum(v);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
   }
   __syncthreads();
-  if (threadIdx.x < nrhs) {
-    double s = 0.0;
-    for (int q = 0; q < kRedThreads / 32; ++q) s += red[q][threadIdx.x];
-    partials[blockIdx.x * kMaxRhs + threadIdx.x] = s;
+  return t;  // valid in warp 0
+}
+
+__device__ __forceinline__ void chunk_of(int64_t len, int64_t& b, int64_t& e) {
+  const int64_t per = (len + gridDim.x - 1) / gridDim.x;
+  b = (int64_t)blockIdx.x * per;
+  e = b + per < len ? b + per : len;
+}
+
+__device__ void apply_op(PcgScalars* s, int k, double sum, int op, double tol2) {
+  if (!isfinite(sum)) {
+    atomicOr(&s->flags, kErrNonFinite);
+    s->conv[k] = 1;
+    s->alpha[k] = 0.0;
+    return;
+  }
+  switch (op) {
+    case kOpBnorm:
+      s->bnorm2[k] = sum;
+      s->conv[k] = sum == 0.0;
+      s->iters[k] = 0;
+      s->rr[k] = sum;
+      break;
+    case kOpRzInit:
+      s->rz[k] = sum;
+      break;
+    case kOpPAp:
+      if (s->conv[k]) {
+        s->alpha[k] = 0.0;
+      } else if (!(sum > 0.0)) {
+        atomicOr(&s->flags, kErrNotSPD);
+        s->conv[k] = 1;
+        s->alpha[k] = 0.0;
+      } else {
+        s->alpha[k] = s->rz[k] / sum;
+      }
+      break;
+    case kOpRR:
+      if (!s->conv[k]) {
+        s->rr[k] = sum;
+        s->iters[k] += 1;
+        if (sum <= tol2 * s->bnorm2[k]) s->conv[k] = 1;
+      }
+      break;
+    case kOpRz:
+      s->beta[k] = s->conv[k] ? 0.0 : sum / s->rz[k];
+      s->rz[k] = sum;
+      break;
   }
 }
 
-// Last block: sum partials in block order and apply op to the scalars.
-__device__ void finalize(PcgScalars* s, const double* __restrict__ partials, int nrhs, int op, double tol2) {
+// Write this block's partial; the last block to arrive reduces all partials
+// of every right-hand side in a fixed order and updates the scalars.
+__device__ void finalize(PcgScalars* s, double* __restrict__ partials, double my_partial, int nrhs, int op,
+                         double tol2) {
   __shared__ bool last;
-  __threadfence();
-  if (threadIdx.x == 0) last = atomicInc(&s->counter, gridDim.x - 1) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.y * kMaxRedBlocks + blockIdx.x] = my_partial;
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    last = atomicInc(&s->counter, total - 1) == total - 1;
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < 32) {
-    const int k = threadIdx.x;
-    double sum = 0.0;
-    if (k < nrhs)
-      for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile const double*)partials)[b * kMaxRhs + k];
-    bool conv_k = true;
-    if (k < nrhs) {
-      if (!isfinite(sum)) {
-        atomicOr(&s->flags, kErrNonFinite);
-        s->conv[k] = 1;
-      } else if (op == kOpBnorm) {
-        s->bnorm2[k] = sum;
-        s->conv[k] = sum == 0.0;
-        s->iters[k] = 0;
-        s->rr[k] = sum;
-      } else if (op == kOpRzInit) {
-        s->rz[k] = sum;
-      } else if (op == kOpPAp) {
-        if (!s->conv[k]) {
-          if (!(sum > 0.0)) {
-            atomicOr(&s->flags, kErrNotSPD);
-            s->conv[k] = 1;
-            s->alpha[k] = 0.0;
-          } else {
-            s->alpha[k] = s->rz[k] / sum;
-          }
-        } else {
-          s->alpha[k] = 0.0;
-        }
-      } else if (op == kOpRR) {
-        if (!s->conv[k]) {
-          s->rr[k] = sum;
-          s->iters[k] += 1;
-          if (sum <= tol2 * s->bnorm2[k]) s->conv[k] = 1;
-        }
-      } else if (op == kOpRz) {
-        s->beta[k] = s->conv[k] ? 0.0 : sum / s->rz[k];
-        s->rz[k] = sum;
-      }
-      conv_k = s->conv[k] != 0;
-    }
-    const bool all = __all_sync(kFull, conv_k);
-    if (k == 0 && (op == kOpRR || op == kOpBnorm || op == kOpPAp)) s->all_conv = all ? 1 : 0;
+  for (int k = 0; k < nrhs; ++k) {
+    double v = 0.0;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += blockDim.x) v += __ldcg(&partials[k * kMaxRedBlocks + g]);
+    const double sum = block_sum(v);
+    if (threadIdx.x == 0) apply_op(s, k, sum, op, tol2);
+  }
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int k = 0; k < nrhs; ++k) all &= s->conv[k] != 0;
+    s->all_conv = all;
   }
 }
 
-// Generic dot a_k . b_k for all RHS; kCopy also writes dst = b (p = z).
+// a_k . b_k per right-hand side; kCopy also writes dst = b (p = z).
 template <bool kCopy>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const double* __restrict__ a, const double* __restrict__ b,
                                                      double* __restrict__ dst, int64_t len, int nrhs,
                                                      PcgScalars* s, double* __restrict__ partials, int op) {
   if (s->all_conv && op != kOpBnorm && op != kOpRzInit) return;
-  double v[kMaxRhs];
-  for (int k = 0; k < nrhs; ++k) v[k] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int k = 0; k < nrhs; ++k) {
-      double bb = b[k * len + i];
-      v[k] += a[k * len + i] * bb;
-      if (kCopy) dst[k * len + i] = bb;
-    }
+  const int64_t o = (int64_t)blockIdx.y * len;
+  int64_t i0, i1;
+  chunk_of(len, i0, i1);
+  double v = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double bb = b[o + i];
+    v += a[o + i] * bb;
+    if (kCopy) dst[o + i] = bb;
   }
-  block_partials(v, nrhs, partials);
-  finalize(s, partials, nrhs, op, 0.0);
+  finalize(s, partials, block_sum(v), nrhs, op, 0.0);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_init(const double* __restrict__ bvec, double* __restrict__ x,
                                                       double* __restrict__ r, int64_t len, int nrhs, PcgScalars* s,
                                                       double* __restrict__ partials) {
-  double v[kMaxRhs];
-  for (int k = 0; k < nrhs; ++k) v[k] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int k = 0; k < nrhs; ++k) {
-      double bb = bvec[k * len + i];
-      x[k * len + i] = 0.0;
-      r[k * len + i] = bb;
-      v[k] += bb * bb;
-    }
+  const int64_t o = (int64_t)blockIdx.y * len;
+  int64_t i0, i1;
+  chunk_of(len, i0, i1);
+  double v = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double bb = bvec[o + i];
+    x[o + i] = 0.0;
+    r[o + i] = bb;
+    v += bb * bb;
   }
-  block_partials(v, nrhs, partials);
-  finalize(s, partials, nrhs, kOpBnorm, 0.0);
+  finalize(s, partials, block_sum(v), nrhs, kOpBnorm, 0.0);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(double* __restrict__ x, double* __restrict__ r,
@@ -156,35 +183,33 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(double* __restrict__ 
                                                            int64_t len, int nrhs, PcgScalars* s,
                                                            double* __restrict__ partials, double tol2) {
   if (s->all_conv) return;
-  double v[kMaxRhs];
-  double al[kMaxRhs];
-  for (int k = 0; k < nrhs; ++k) v[k] = 0.0, al[k] = s->alpha[k];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int k = 0; k < nrhs; ++k) {
-      const int64_t o = k * len + i;
-      double rk = r[o];
-      if (al[k] != 0.0) {
-        x[o] += al[k] * p[o];
-        rk -= al[k] * Ap[o];
-        r[o] = rk;
-      }
-      v[k] += rk * rk;
+  const int k = blockIdx.y;
+  const double al = s->alpha[k];
+  const int64_t o = (int64_t)k * len;
+  int64_t i0, i1;
+  chunk_of(len, i0, i1);
+  double v = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double rk = r[o + i];
+    if (al != 0.0) {
+      x[o + i] += al * p[o + i];
+      rk -= al * Ap[o + i];
+      r[o + i] = rk;
     }
+    v += rk * rk;
   }
-  block_partials(v, nrhs, partials);
-  finalize(s, partials, nrhs, kOpRR, tol2);
+  finalize(s, partials, block_sum(v), nrhs, kOpRR, tol2);
 }
 
-__global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, int64_t len, int nrhs,
-                           const PcgScalars* s) {
-  if (s->all_conv) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int k = 0; k < nrhs; ++k) {
-      if (s->conv[k]) continue;
-      const int64_t o = k * len + i;
-      p[o] = z[o] + s->beta[k] * p[o];
-    }
-  }
+__global__ void __launch_bounds__(kRedThreads) k_update_p(double* __restrict__ p, const double* __restrict__ z,
+                                                          int64_t len, const PcgScalars* s) {
+  const int k = blockIdx.y;
+  if (s->all_conv || s->conv[k]) return;
+  const double be = s->beta[k];
+  const int64_t o = (int64_t)k * len;
+  int64_t i0, i1;
+  chunk_of(len, i0, i1);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) p[o + i] = z[o + i] + be * p[o + i];
 }
 
 }  // namespace gs
@@ -207,7 +232,7 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   GS_TRY(ctx->scratch_buf(kSlotPcgVectors, 4 * vbytes, (void**)&vec));
   double *r = vec, *z = r + nrhs * len, *p = z + nrhs * len, *Ap = p + nrhs * len;
   char* sbuf = nullptr;
-  GS_TRY(ctx->scratch_buf(kSlotPcgScalars, sizeof(PcgScalars) + kRedBlocks * kMaxRhs * sizeof(double) + 256,
+  GS_TRY(ctx->scratch_buf(kSlotPcgScalars, sizeof(PcgScalars) + kMaxRedBlocks * kMaxRhs * sizeof(double) + 256,
                           (void**)&sbuf));
   PcgScalars* s = (PcgScalars*)sbuf;
   double* partials = (double*)(sbuf + ((sizeof(PcgScalars) + 255) / 256) * 256);
@@ -217,19 +242,20 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   if (variant == GS_SPMV_ROW) GS_TRY(ensure_lower(ctx, mat));  // built once per matrix
 
   const double tol2 = tol * tol;
-  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_init<<<kRedBlocks, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials); }
+  const dim3 vg(red_blocks(len), nrhs);
+  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_init<<<vg, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials); }
   GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
-  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<true><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit); }
+  { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<true><<<vg, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit); }
   const int poll = 4;
   int* h_conv = ctx->h_pinned + 64;
   for (int it = 0; it < max_iter; ++it) {
     GS_TRY(spmv_launch(ctx, mat, p, Ap, nrhs, variant));
-    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp); }
-    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_xr<<<kRedBlocks, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<vg, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_xr<<<vg, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2); }
     if (it + 1 == max_iter) break;
     GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
-    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<kRedBlocks, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz); }
-    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_p<<<kRedBlocks * 4, kRedThreads, 0, st>>>(p, z, len, nrhs, s); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<vg, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_p<<<vg, kRedThreads, 0, st>>>(p, z, len, s); }
     if ((it + 1) % poll == 0) {
       GS_CUDA(cudaMemcpyAsync(h_conv, &s->all_conv, 4, cudaMemcpyDeviceToHost, st));
       GS_CUDA(cudaStreamSynchronize(st));

@@ -48,14 +48,14 @@ __global__ void __launch_bounds__(256) k_spmv_srbk(const int32_t* __restrict__ r
         if (b != j) {
           double xb0 = xr[3 * b], xb1 = xr[3 * b + 1], xb2 = xr[3 * b + 2];
           double* yr = y + r * stride + 3 * j;
-          atomicAdd(yr + 0, H[0] * xb0 + H[3] * xb1 + H[6] * xb2);
-          atomicAdd(yr + 1, H[1] * xb0 + H[4] * xb1 + H[7] * xb2);
-          atomicAdd(yr + 2, H[2] * xb0 + H[5] * xb1 + H[8] * xb2);
+          atomicAdd(yr + 0, fma(H[6], xb2, fma(H[3], xb1, H[0] * xb0)));
+          atomicAdd(yr + 1, fma(H[7], xb2, fma(H[4], xb1, H[1] * xb0)));
+          atomicAdd(yr + 2, fma(H[8], xb2, fma(H[5], xb1, H[2] * xb0)));
         }
       }
-      v[3 * q + 0] = H[0] * xj0 + H[1] * xj1 + H[2] * xj2;
-      v[3 * q + 1] = H[3] * xj0 + H[4] * xj1 + H[5] * xj2;
-      v[3 * q + 2] = H[6] * xj0 + H[7] * xj1 + H[8] * xj2;
+      v[3 * q + 0] = fma(H[2], xj2, fma(H[1], xj1, H[0] * xj0));
+      v[3 * q + 1] = fma(H[5], xj2, fma(H[4], xj1, H[3] * xj0));
+      v[3 * q + 2] = fma(H[8], xj2, fma(H[7], xj1, H[6] * xj0));
     }
     head_segmented_reduce<kR * 3>(v, lane, send);
     if (head && in) {
@@ -72,11 +72,10 @@ __global__ void __launch_bounds__(256) k_spmv_srbk(const int32_t* __restrict__ r
   }
 }
 
-// Eight lanes per block row; each lane strides over the row's entries
-// (its upper blocks first, then its transposed references).
-constexpr int kRowLanes = 8;
-
-template <int kR>
+// kLanes lanes per block row; each lane strides over the row's entries
+// (its upper blocks first, then its transposed references) and keeps kR
+// right-hand sides in registers, so every block is loaded once per kR RHS.
+template <int kLanes, int kR>
 __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
                                                   const int32_t* __restrict__ lo_ptr,
                                                   const int32_t* __restrict__ lo_idx,
@@ -84,8 +83,8 @@ __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ ro
                                                   int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
                                                   double* __restrict__ y) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t row = (int32_t)(t / kRowLanes);
-  int sub = threadIdx.x % kRowLanes;
+  int32_t row = (int32_t)(t / kLanes);
+  int sub = threadIdx.x % kLanes;
   bool in = row < n;
   int32_t u0 = 0, u1 = 0, l0 = 0, l1 = 0;
   if (in) {
@@ -97,7 +96,7 @@ __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ ro
     double acc[kR * 3];
 #pragma unroll
     for (int k = 0; k < kR * 3; ++k) acc[k] = 0.0;
-    for (int32_t e = sub; e < total; e += kRowLanes) {
+    for (int32_t e = sub; e < total; e += kLanes) {
       bool upper = e < nu;
       int64_t blk;
       int32_t col;
@@ -120,17 +119,21 @@ __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ ro
       for (int q = 0; q < kR; ++q) {
         if (r0 + q < nrhs) {
           const double* xr = x + (r0 + q) * stride + 3 * col;
-          double x0 = xr[0], x1 = xr[1], x2 = xr[2];
-          acc[3 * q + 0] += H[0] * x0 + H[1] * x1 + H[2] * x2;
-          acc[3 * q + 1] += H[3] * x0 + H[4] * x1 + H[5] * x2;
-          acc[3 * q + 2] += H[6] * x0 + H[7] * x1 + H[8] * x2;
+          const double x0 = xr[0], x1 = xr[1], x2 = xr[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            double a = acc[3 * q + c];
+            a = fma(H[3 * c + 0], x0, a);
+            a = fma(H[3 * c + 1], x1, a);
+            acc[3 * q + c] = fma(H[3 * c + 2], x2, a);
+          }
         }
       }
     }
 #pragma unroll
     for (int k = 0; k < kR * 3; ++k) {
 #pragma unroll
-      for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o, kRowLanes);
+      for (int o = kLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(kFull, acc[k], o, kLanes);
     }
     if (in && sub == 0) {
 #pragma unroll
@@ -221,13 +224,22 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
       { GS_PROF(ctx, GS_K_SPMV); k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y); }
   } else {
     GS_TRY(ensure_lower(ctx, m));
-    const int64_t threads = (int64_t)m->n * kRowLanes;
-    if (nrhs == 1)
-      { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
-                                                            m->au, m->n, stride, nrhs, x, y); }
-    else
-      { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4><<<ceil_div(threads, 256), 256, 0, st>>>(m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col,
-                                                            m->au, m->n, stride, nrhs, x, y); }
+    // lanes per row x RHS per pass (ctx->spmv_cfg: 0 = 2x8, 1 = 8x4, 2 = 4x8)
+    const int cfg = ctx->spmv_cfg;
+    const int lanes = cfg == 1 ? 8 : (cfg == 2 ? 4 : 2);
+    const int64_t threads = (int64_t)m->n * lanes;
+    const int grid = ceil_div(threads, 256);
+#define GS_ROW_ARGS m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col, m->au, m->n, stride, nrhs, x, y
+    if (nrhs == 1) {
+      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+    } else {
+      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 4><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+    }
+#undef GS_ROW_ARGS
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;

@@ -119,7 +119,22 @@ def _generator_device():
     return "cuda" if torch.cuda.is_available() else "cpu"
 
 
-def snh_element_blocks(X, x, tets, E, nu, chunk=400_000, device=None):
+def _element_chunk(X, x, t, swap, E, nu, pa, pb, device):
+    F, vol, w = deformation_gradient(X, x, t)
+    Ft = torch.from_numpy(F).to(device)
+    _, _, HF = snh_energy_grad_hess_F(Ft, E, nu)
+    P = _psd_project(HF).reshape(-1, 3, 3, 3, 3)  # [t, i, x, j, y] (F column i, comp x)
+    wt = torch.from_numpy(w).to(device)
+    He = torch.einsum("tai,tixjy->taxjy", wt, P)
+    He = torch.einsum("tbj,taxjy->tabxy", wt, He)
+    He = He * torch.from_numpy(vol).to(device)[:, None, None, None, None]
+    blk = He[:, pa, pb]  # (t, 10, 3, 3)
+    sw = torch.from_numpy(swap).to(device)
+    blk = torch.where(sw[:, :, None, None], blk.transpose(-1, -2), blk)
+    return blk.cpu().numpy()
+
+
+def snh_element_blocks(X, x, tets, E, nu, chunk=None, device=None):
     """Upper-triangle 3x3 blocks of the PSD-projected SNH Hessian per tet.
 
     Returns rows (K,), cols (K,), blocks (K, 3, 3) with K = 10 * T, in
@@ -127,6 +142,8 @@ def snh_element_blocks(X, x, tets, E, nu, chunk=400_000, device=None):
     (on the GPU when one is present); only the inputs depend on this.
     """
     device = device or _generator_device()
+    if chunk is None:
+        chunk = 32_768 if device == "cuda" else 400_000  # batched eigh sizes the solver accepts
     T = tets.shape[0]
     pa = np.array([p[0] for p in _PAIRS])
     pb = np.array([p[1] for p in _PAIRS])
@@ -136,20 +153,17 @@ def snh_element_blocks(X, x, tets, E, nu, chunk=400_000, device=None):
     rows = np.where(swap, cb, ra).astype(np.int32).ravel()
     cols = np.where(swap, ra, cb).astype(np.int32).ravel()
     blocks = np.empty((T, 10, 3, 3))
-    for s in range(0, T, chunk):
-        t = tets[s : s + chunk]
-        F, vol, w = deformation_gradient(X, x, t)
-        Ft = torch.from_numpy(F).to(device)
-        _, _, HF = snh_energy_grad_hess_F(Ft, E, nu)
-        P = _psd_project(HF).reshape(-1, 3, 3, 3, 3)  # [t, i, x, j, y] (F column i, comp x)
-        wt = torch.from_numpy(w).to(device)
-        He = torch.einsum("tai,tixjy->taxjy", wt, P)
-        He = torch.einsum("tbj,taxjy->tabxy", wt, He)
-        He = He * torch.from_numpy(vol).to(device)[:, None, None, None, None]
-        blk = He[:, pa, pb]  # (t, 10, 3, 3)
-        sw = torch.from_numpy(swap[s : s + chunk]).to(device)
-        blk = torch.where(sw[:, :, None, None], blk.transpose(-1, -2), blk)
-        blocks[s : s + chunk] = blk.cpu().numpy()
+    s = 0
+    while s < T:
+        try:
+            blocks[s : s + chunk] = _element_chunk(X, x, tets[s : s + chunk], swap[s : s + chunk], E, nu, pa, pb,
+                                                   device)
+        except RuntimeError:
+            if device == "cpu":
+                raise
+            device, chunk = "cpu", 400_000  # the GPU solver is unavailable here: finish on the host
+            continue
+        s += chunk
     return rows, cols, blocks.reshape(-1, 3, 3)
 
 
