@@ -169,6 +169,22 @@ int gs_mas_export_inverse(gs_ctx ctx, gs_mas mas, int32_t level, double* inv);
 /* z = M^{-1} r = sum_l C_l^T M_l^{-1} C_l r (supplement Eq. 6) for nrhs
  * right-hand sides; r, z device double[nrhs * 3n], not overlapping. */
 int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs);
+/* The same apply with no device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * once they are running -- an application that gives the library a fixed
+ * memory budget at start-up, where a later cudaMalloc could fail under the
+ * cap or stall every stream on the device while memory is mapped.  The
+ * coarse-level scratch that gs_mas_apply takes from the memory pool lives
+ * here in a fixed 4 MiB array compiled into the library, held by every GPU
+ * that loads it until the process exits.
+ * Arguments and result: as gs_mas_apply.  Limit: 2 * nrhs * 3 * (items of
+ * all levels >= 1, domains padded to N) doubles must not exceed 524,288;
+ * otherwise GS_ERR_INVALID with a message naming the sizes.
+ * The first call on each device looks the array's address up (with that
+ * device current) and should be made before any stream capture begins.
+ * Calls share the array and clear its restricted part on entry; calls whose
+ * work overlaps on the GPU race on it. */
+int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs);
 int gs_mas_destroy(gs_mas mas);
 
 /* ---------------------------------------------------------------- PCG */

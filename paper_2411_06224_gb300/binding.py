@@ -61,6 +61,7 @@ EXPORTS = [
     "gs_mas_export_coarse",
     "gs_mas_export_inverse",
     "gs_mas_apply",
+    "gs_mas_apply_noalloc",
     "gs_mas_destroy",
     "gs_pcg_solve",
     "gs_profile_begin",
@@ -119,6 +120,7 @@ def lib():
             "gs_mas_export_coarse": (ctypes.c_int, [_P, _P, _I32, _P]),
             "gs_mas_export_inverse": (ctypes.c_int, [_P, _P, _I32, _P]),
             "gs_mas_apply": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+            "gs_mas_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
             "gs_mas_destroy": (ctypes.c_int, [_P]),
             "gs_pcg_solve": (ctypes.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _I32, _P, _P, _P]),
             "gs_profile_begin": (ctypes.c_int, [_P, ctypes.c_uint32]),

@@ -1,0 +1,80 @@
+// gs_mas_apply_noalloc: the MAS apply without any device allocation.
+//
+// gs_mas_apply keeps the restricted and coarse-level vectors of an apply in
+// a scratch buffer that the context grows on demand from the CUDA memory
+// pool.  Some callers cannot allow that: a host application that hands the
+// library a fixed device-memory budget at start-up and forbids any later
+// cudaMalloc (an allocation there can fail under the cap, or stall every
+// stream on the device while the driver maps memory), or code that must
+// not allocate at all once it is running.  This entry point keeps that
+// scratch in a fixed array compiled into the library instead.
+//
+// The array is a file-scope __device__ symbol of kNoAllocDoubles doubles
+// (4 MiB).  Every GPU on which the library's module is loaded holds it until
+// the process exits.  Host code cannot use the symbol's name as a device
+// address, so the first call on each device looks the address up with
+// cudaGetSymbolAddress (with that device current) and caches it; that first
+// call per device should therefore be made before any stream capture
+// begins.  All calls share the array: the restricted vectors are cleared at
+// the start of every call, and two calls whose work overlaps on the GPU
+// (different streams, or different threads on one device) race on it.
+// With the profiler switched on (gs_profile_begin) the library may create
+// CUDA events; it is off unless the caller turns it on.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace gs {
+constexpr size_t kNoAllocDoubles = size_t(1) << 19;  // 4 MiB of float64
+}
+
+// The fixed scratch: restricted vectors (first half of the used part) and
+// coarse-level results (second half) of one apply.
+static __device__ __align__(256) double g_level_scratch[gs::kNoAllocDoubles];
+
+namespace gs {
+
+int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+std::mutex g_lock;
+double* g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (current), looked up once.
+int scratch_address(int device, double** out) {
+  std::lock_guard<std::mutex> guard(g_lock);
+  if (!g_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_level_scratch);
+    if (e != cudaSuccess) {
+      set_error("gs_mas_apply_noalloc: cudaGetSymbolAddress failed on device %d: %s", device,
+                cudaGetErrorString(e));
+      return GS_ERR_CUDA;
+    }
+    g_addr[device] = (double*)p;
+  }
+  *out = g_addr[device];
+  return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs) {
+  GS_CHECK(ctx && mas && r && z && r != z, GS_ERR_INVALID, "gs_mas_apply_noalloc: null or aliased argument");
+  GS_CHECK(nrhs >= 1, GS_ERR_INVALID, "gs_mas_apply_noalloc: nrhs %d", nrhs);
+  GS_CHECK(ctx->device >= 0 && ctx->device < gs::kMaxDevices, GS_ERR_UNSUPPORTED,
+           "gs_mas_apply_noalloc: device %d", ctx->device);
+  const size_t per = (size_t)nrhs * 3 * (size_t)std::max<int64_t>(mas->vec_items, 1);
+  GS_CHECK(2 * per <= gs::kNoAllocDoubles, GS_ERR_INVALID,
+           "gs_mas_apply_noalloc: needs %zu doubles of coarse-level scratch (2 x %d RHS x 3 x %lld items), "
+           "above the fixed %zu; use gs_mas_apply",
+           2 * per, nrhs, (long long)mas->vec_items, gs::kNoAllocDoubles);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  double* base = nullptr;
+  GS_TRY(gs::scratch_address(ctx->device, &base));
+  return gs::mas_apply_launch(ctx, mas, r, z, nrhs, base, base + per);
+}
