@@ -398,3 +398,85 @@ def test_pcg_fixed_iterations_and_zero_rhs():
     assert it[1] == 3
     # after 3 steps the residual is smaller than at the start
     assert np.linalg.norm(b[1] - A @ x[1]) < np.linalg.norm(b[1])
+
+
+# ---------------------------------------------------------------- adjoint (gradients through the solve)
+def test_adjoint_gradients_match_central_differences():
+    from oracle import adjoint
+
+    s = _tiny_system(n=4, E=1e5, contacts=5, seed=9)
+    rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
+    n = s.n_vertices
+    rng = np.random.default_rng(10)
+    b = rng.normal(size=(2, 3 * n))
+    xt = rng.normal(size=(2, 3 * n)) * 1e-3
+
+    def L_of(bb, aa):
+        x = adjoint.solve_dense(n, rid, cid, aa, bb)
+        return adjoint.loss_and_grad(x, xt)[0]
+
+    x = adjoint.solve_dense(n, rid, cid, au, b)
+    _, g = adjoint.loss_and_grad(x, xt)
+    lam = adjoint.solve_dense(n, rid, cid, au, g)
+    G = adjoint.block_gradients(rid, cid, x, lam)
+    # along b
+    db = rng.normal(size=b.shape)
+    eps = 1e-6 * np.linalg.norm(b) / np.linalg.norm(db)
+    fd = (L_of(b + eps * db, au) - L_of(b - eps * db, au)) / (2 * eps)
+    assert abs(fd - np.sum(lam * db)) <= 1e-6 * abs(fd)
+    # along the stored blocks (each perturbation symmetric through the storage)
+    dH = rng.normal(size=au.shape)
+    eps = 1e-6 * np.linalg.norm(au) / np.linalg.norm(dH)
+    fd = (L_of(b, au + eps * dH) - L_of(b, au - eps * dH)) / (2 * eps)
+    assert abs(fd - np.sum(G * dH)) <= 1e-5 * abs(fd)
+
+
+# ---------------------------------------------------------------- cubic strain-limiting energy (Sec. 4)
+def _random_F(rng, stretch):
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    S = np.array([[stretch[0], rng.uniform(-0.05, 0.05)], [0.0, stretch[1]]])
+    return Q[:, :2] @ S
+
+
+@pytest.mark.parametrize("stretch", [(1.08, 0.97), (1.3, 1.2), (0.9, 1.15)])
+def test_strain_limit_gradient_and_hessian_by_differences(stretch):
+    from oracle import strain_limit as sl
+
+    rng = np.random.default_rng(int(100 * stretch[0]))
+    F = _random_F(rng, stretch)
+    for n in (sl.N_U, sl.N_V):
+        f = F.T.reshape(6)  # vec(F), columns stacked
+        E = lambda v: sl.energy(v.reshape(2, 3).T, n)
+        G = lambda v: sl.gradient(v.reshape(2, 3).T, n)
+        h = 1e-6
+        g_fd = np.array([(E(f + h * e) - E(f - h * e)) / (2 * h) for e in np.eye(6)])
+        np.testing.assert_allclose(sl.gradient(F, n), g_fd, rtol=1e-6, atol=1e-9)
+        H_fd = np.stack([(G(f + h * e) - G(f - h * e)) / (2 * h) for e in np.eye(6)], 1)
+        np.testing.assert_allclose(sl.hessian(F, n), H_fd, rtol=1e-5, atol=1e-7)
+
+
+def test_strain_limit_eigensystem_closed_forms():
+    from oracle import strain_limit as sl
+
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        F = _random_F(rng, rng.uniform(1.01, 1.5, 2))
+        for n in (sl.N_U, sl.N_V):
+            w = np.sort(np.linalg.eigvalsh(sl.hessian(F, n)))
+            e1, e2, e3 = sl.eigenvalues(F, n)
+            # the direction-n block has e1, e2, e3; the other direction's block is zero
+            np.testing.assert_allclose(w[-3:], np.sort([e1, e2, e3]), rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(w[:3], 0.0, atol=1e-12)
+            assert min(e1, e2) > 0  # convex when stretched
+
+
+def test_strain_limit_is_c2_at_the_limit():
+    from oracle import strain_limit as sl
+
+    F = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    for eps in (1e-3, 1e-5):
+        Fe = F * (1.0 + eps)
+        assert sl.energy(Fe, sl.N_U) < 2 * eps ** 3
+        assert np.abs(sl.gradient(Fe, sl.N_U)).max() < 4 * eps ** 2
+        assert np.abs(sl.hessian(Fe, sl.N_U)).max() < 20 * eps
+    assert sl.energy(F * 0.9, sl.N_U) == 0.0 and not sl.hessian(F * 0.9, sl.N_U).any()
