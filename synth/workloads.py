@@ -135,3 +135,49 @@ def stiffness_sweep(Es=(1e5, 1e7, 1e9), n=64, seed=1002):
     (scaled with the vertex count for other n); 3-level MAS, N=32."""
     return make_tet_systems(n, Es, n_contacts=max(1, 200_000 * n ** 3 // 64 ** 3),
                             contact_mode="near", seed=seed)
+
+
+@dataclass
+class Batch:
+    """Independent systems concatenated as the diagonal blocks of one matrix."""
+
+    systems: list
+    node_off: np.ndarray  # int32 (S + 1,)
+    X: np.ndarray
+    rows: np.ndarray
+    cols: np.ndarray
+    blocks: np.ndarray
+    adj_ptr: np.ndarray
+    adj: np.ndarray
+    contacts: np.ndarray
+
+    @property
+    def n_vertices(self):
+        return int(self.node_off[-1])
+
+
+def concat_systems(systems):
+    off = np.concatenate([[0], np.cumsum([s.n_vertices for s in systems])]).astype(np.int32)
+    rows = np.concatenate([s.rows + o for s, o in zip(systems, off)]).astype(np.int32)
+    cols = np.concatenate([s.cols + o for s, o in zip(systems, off)]).astype(np.int32)
+    blocks = np.concatenate([s.blocks for s in systems])
+    eoff = np.concatenate([[0], np.cumsum([s.adj.size for s in systems])])
+    adj_ptr = np.concatenate([s.adj_ptr[:-1] + e for s, e in zip(systems, eoff)] + [[eoff[-1]]]).astype(np.int32)
+    adj = np.concatenate([s.adj + o for s, o in zip(systems, off)]).astype(np.int32)
+    contacts = np.concatenate([s.contacts.reshape(-1, 2) + o for s, o in zip(systems, off)]).astype(np.int32)
+    X = np.concatenate([s.X for s in systems])
+    return Batch(systems, off, X, rows, cols, blocks, adj_ptr, adj, contacts)
+
+
+def uneven_batch(n_sys=64, v_range=(1_000, 50_000), e_range=(1e5, 1e9), contact_frac=0.05, seed=1004):
+    """n_sys tet cubes with vertex counts log-uniform in v_range (n = round(V^(1/3))),
+    E log-uniform in e_range and random contact pairs on contact_frac of the vertices."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    for s in range(n_sys):
+        V = np.exp(rng.uniform(np.log(v_range[0]), np.log(v_range[1])))
+        n = max(3, int(round(V ** (1.0 / 3.0))))
+        E = float(np.exp(rng.uniform(np.log(e_range[0]), np.log(e_range[1]))))
+        systems.append(make_tet_system(n, E=E, n_contacts=max(1, int(contact_frac * n ** 3)),
+                                       contact_mode="random", seed=seed * 1000 + s))
+    return concat_systems(systems)
