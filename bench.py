@@ -32,6 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300: derived from the nominal 1.25 TFLOP/s FP64 at 2.07 GHz, 152 SMs
+# DRAM bytes of one level-0 apply launch per domain at 8 RHS (FP64), from the
+# ncu capture on the 40^3 case (profiles/k_domain_product_fp64_tet40.md):
+# 172.9 MB over 2000 domains; traffic grows with the domain count.
+APPLY_DRAM_BYTES_PER_DOMAIN_8RHS = 172.9e6 / 2000
 TOL = 1e-6
 METRIC = "Newton solves/s to 1e-6 rel. residual (FP64 MAS-PCG)"
 
@@ -47,7 +51,13 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--spmv", default="row", choices=["row", "srbk"])
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the default launch shapes instead of tuning them first")
+    p.add_argument("--batch-steps", type=int, default=2, help="timed steps of the batched form (64 uneven systems)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--micro", action="store_true",
+                   help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
     p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)  # worker mode
     return p.parse_args()
 
@@ -144,6 +154,12 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workload on the GPU
+def autotune_current(B, ctx):
+    from paper_2411_06224_gb300 import autotune
+
+    return autotune.current(ctx)
+
+
 def make_workload(grid, nrhs, rank):
     import numpy as np
 
@@ -164,6 +180,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.micro:
+        return micro(args)
 
     import numpy as np
     import torch
@@ -214,6 +232,31 @@ def main():
         if world > 1:
             dist.barrier()
 
+    # launch shapes: the autotuner times each candidate on the stiffest system
+    # (outside the timed region) and leaves the fastest set in the context
+    tuned = None
+    if args.autotune:
+        from paper_2411_06224_gb300 import autotune
+
+        s = dsys[-1]
+        mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
+        mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
+                             domain_size=N, max_levels=L, precision=prec)
+        res = autotune.tune(ctx, mat, mas, nrhs=args.nrhs, reps=5, mixed=args.mixed_steps > 0)
+        B.gs_mas_destroy(mas)
+        if args.mixed_steps > 0 and args.nrhs <= 8:  # BF16 level-0 product: tensor cores or FP32 cores
+            mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
+                                 domain_size=N, max_levels=L, precision=B.GS_PREC_BF16)
+            xr = torch.randn((args.nrhs, 3 * V), dtype=torch.float64, device=dev)
+            yr = torch.empty_like(xr)
+            res[autotune.NAMES[B.GS_TUNE_BF16_TC]] = autotune.sweep(
+                ctx, B.GS_TUNE_BF16_TC, B.GS_K_MAS_APPLY_L0, lambda: B.gs_mas_apply(ctx, mas, xr, yr, nrhs=args.nrhs),
+                reps=5)
+            B.gs_mas_destroy(mas)
+        tuned = {k: {"best": v[0], "ms_per_launch": {str(c): round(m, 4) for c, m in v[1].items()}}
+                 for k, v in res.items()}
+        B.gs_mat_destroy(mat)
+
     # warm-up
     for _ in range(args.warmup):
         warm = step()
@@ -244,13 +287,10 @@ def main():
     launches, kms = B.gs_profile_end(ctx)
     barrier()
     clk = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    solves = len(dsys) * args.steps * world
-    value = solves / elapsed
+    from paper_2411_06224_gb300 import replicas
+
+    # independent replicas: every rank solved its own systems; the slowest rank sets the time
+    value, elapsed = replicas.throughput(len(dsys) * args.steps, e0.elapsed_time(e1) / 1e3, dev)
 
     # true residuals of the last step (checked on the device through the library's SpMV)
     true_rel = []
@@ -287,13 +327,143 @@ def main():
                 hx.copy_(xx, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        el = f0.elapsed_time(f1) / 1e3
-        if world > 1:
-            tt = torch.tensor([el], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
-        e2e = {"value": len(hsys) * args.e2e_steps * world / el, "unit": "Newton solves/s",
+        e2e_rate, el = replicas.throughput(len(hsys) * args.e2e_steps, f0.elapsed_time(f1) / 1e3, dev)
+        e2e = {"value": e2e_rate, "unit": "Newton solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # the mixed-precision forms on the same workload and right-hand sides:
+    #   f64_pcg_f32_mas   FP64 PCG, MAS inverses stored and applied in FP32
+    #   f64_pcg_bf16_mas  FP64 PCG, BF16 inverses, level-0 product on the tensor cores
+    #   f32_inner_pcg     FP32 PCG (FP32 SpMV + FP32 MAS) with FP64 reliable updates
+    mixed = None
+    if args.mixed_steps > 0 and args.nrhs <= 8:
+        x_fp64 = x.clone()  # FP64 solution of the last system (last timed step)
+        variants = [("f64_pcg_f32_mas", B.GS_PREC_FP32, False), ("f64_pcg_bf16_mas", B.GS_PREC_BF16, False),
+                    ("f32_inner_pcg", B.GS_PREC_FP32, True)]
+        mixed = {}
+        def run_variant(vprec, inner32):
+            def mixed_one(s):
+                mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
+                mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"],
+                                     shared["contacts"], domain_size=N, max_levels=L, precision=vprec)
+                try:
+                    if inner32:
+                        it, rel, outer, _ = B.gs_pcg_solve_mixed(ctx, mat, mas, b, x, nrhs=args.nrhs, tol=TOL,
+                                                                 max_iter=20000)
+                    else:
+                        it, rel, _ = B.gs_pcg_solve(ctx, mat, mas, b, x, nrhs=args.nrhs, tol=TOL, max_iter=20000,
+                                                    variant=variant)
+                        outer = None
+                finally:
+                    B.gs_mas_destroy(mas)
+                    B.gs_mat_destroy(mat)
+                return [int(v) for v in it], [float(v) for v in rel], outer
+
+            for s in dsys:  # warm-up, one solve per system
+                mixed_one(s)
+            barrier()
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            mres = []
+            for _ in range(args.mixed_steps):
+                mres = [mixed_one(s) for s in dsys]
+            g1.record(stream)
+            torch.cuda.synchronize()
+            mrate, mel = replicas.throughput(len(dsys) * args.mixed_steps, g0.elapsed_time(g1) / 1e3, dev)
+            # true residuals of the last system, recomputed in FP64 through the library's SpMV
+            s = dsys[-1]
+            mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
+            B.gs_spmv(ctx, mat, x, Ax, nrhs=args.nrhs, variant=B.GS_SPMV_ROW)
+            B.gs_mat_destroy(mat)
+            return {
+                "value": mrate, "unit": "Newton solves/s", "ms_per_step": mel / args.mixed_steps * 1e3,
+                "steps": args.mixed_steps,
+                "iterations": [r[0] for r in mres], "outer_steps": [r[2] for r in mres],
+                "true_rel_residual_last_system": ((b - Ax).norm(dim=1) / b.norm(dim=1)).tolist(),
+                # both solves stop on the 1e-6 residual test; their distance (last system)
+                "rel_error_vs_fp64_max": float(((x - x_fp64).norm(dim=1) / x_fp64.norm(dim=1)).max()),
+            }
+
+        for name, vprec, inner32 in variants:
+            try:
+                mixed[name] = run_variant(vprec, inner32)
+            except B.GsError as e:  # a form that fails is reported; the main measurement stands
+                mixed[name] = {"error": str(e)[:300]}
+
+    # the batched form: 64 independent uneven tet cubes (1k-50k vertices, E 1e5-1e9,
+    # contacts on 5% of the vertices), one RHS each, solved as one block-diagonal
+    # batch with one PCG recurrence per system and the loop in one CUDA graph;
+    # compared with solving the same systems one after another on the plain path
+    batched = None
+    if args.batch_steps > 0:
+        from synth.workloads import uneven_batch
+
+        bt = uneven_batch(64, seed=1004 + rank)
+        Vb = bt.n_vertices
+        bmap, bnd = B.gs_partition_batch(bt.X, bt.node_off, N)  # once per mesh set, before timing
+        bd = dict(rows=t(bt.rows, torch.int32), cols=t(bt.cols, torch.int32),
+                  blocks=t(bt.blocks.reshape(-1, 3, 3), torch.float64), map=t(bmap, torch.int32),
+                  adj_ptr=t(bt.adj_ptr, torch.int32), adj=t(bt.adj, torch.int32), contacts=t(bt.contacts, torch.int32))
+        bb = t(rhs_batch := np.random.default_rng(3000 + rank).normal(size=3 * Vb), torch.float64)
+        bx = torch.zeros_like(bb)
+
+        def batch_solve(prec_b):
+            mat = B.gs_assemble(ctx, Vb, bd["rows"], bd["cols"], bd["blocks"])
+            mas = B.gs_build_mas(ctx, mat, bd["map"], bnd, bd["adj_ptr"], bd["adj"], bd["contacts"],
+                                 domain_size=N, max_levels=L, precision=prec_b)
+            it, rel, _ = B.gs_pcg_solve_batch(ctx, mat, mas, bt.node_off, bb, bx, tol=TOL, max_iter=20000,
+                                              use_graph=True)
+            B.gs_mas_destroy(mas)
+            B.gs_mat_destroy(mat)
+            return it, rel
+
+        def timed(fn, steps):
+            fn()  # warm-up
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            out = None
+            for _ in range(steps):
+                out = fn()
+            q1.record(stream)
+            torch.cuda.synchronize()
+            return q0.elapsed_time(q1) / 1e3 / steps, out
+
+        tb64, (it64, rel64) = timed(lambda: batch_solve(B.GS_PREC_FP64), args.batch_steps)
+        tb32, (it32, rel32) = timed(lambda: batch_solve(B.GS_PREC_FP32), args.batch_steps)
+        # the same 64 systems one at a time on the plain path
+        seq = []
+        for si, sysb in enumerate(bt.systems):
+            Vs = sysb.n_vertices
+            mps, nds = B.gs_partition(sysb.X, N)
+            seq.append((Vs, t(sysb.rows, torch.int32), t(sysb.cols, torch.int32),
+                        t(sysb.blocks.reshape(-1, 3, 3), torch.float64), t(mps, torch.int32), nds,
+                        t(sysb.adj_ptr, torch.int32), t(sysb.adj, torch.int32), t(sysb.contacts, torch.int32),
+                        t(rhs_batch[3 * bt.node_off[si]:3 * bt.node_off[si + 1]], torch.float64)))
+
+        def sequential():
+            for (Vs, r_, c_, bl_, mp_, nd_, ap_, aj_, ct_, b_) in seq:
+                mat = B.gs_assemble(ctx, Vs, r_, c_, bl_)
+                mas = B.gs_build_mas(ctx, mat, mp_, nd_, ap_, aj_, ct_, domain_size=N, max_levels=L)
+                xs = torch.empty_like(b_)
+                B.gs_pcg_solve(ctx, mat, mas, b_, xs, nrhs=1, tol=TOL, max_iter=20000)
+                B.gs_mas_destroy(mas)
+                B.gs_mat_destroy(mat)
+
+        tseq, _ = timed(sequential, 1)
+        batched = {
+            "workload": "64 tet cubes, vertices log-uniform 1k-50k (%d total), E log-uniform 1e5-1e9, contacts on 5%% of "
+                        "vertices, 1 RHS each, 3-level MAS N=32, tol 1e-6" % Vb,
+            "fp64": {"value": 64 / tb64, "unit": "Newton solves/s", "ms_per_batch": tb64 * 1e3,
+                     "max_iterations": int(max(it64)), "true_rel_residual_max": float(max(rel64))},
+            "fp32_preconditioner": {"value": 64 / tb32, "unit": "Newton solves/s", "ms_per_batch": tb32 * 1e3,
+                                    "max_iterations": int(max(it32))},
+            "sequential_plain_fp64": {"value": 64 / tseq, "unit": "Newton solves/s", "ms_for_64": tseq * 1e3},
+            "graph": "whole PCG loop = one CUDA graph launch (conditional WHILE node)",
+        }
 
     # roofline of the dominant kernel class
     props = torch.cuda.get_device_properties(dev)
@@ -323,8 +493,12 @@ def main():
                 "hbm_gbs": nbytes / tsec / 1e9, "hbm_frac": nbytes / tsec / 1e9 / hbm,
                 "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
 
-    apply_line = fp64_line(apply_flops, apply_bytes, t_apply, None)
-    apply_line["kernel"] = "k_domain_product<double,4,1> (level-0 MAS apply + prolongation)"
+    traffic = (APPLY_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
+               if args.nrhs == 8 and prec == B.GS_PREC_FP64 and N == 32
+               and B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS) == 4 else None)  # the captured shape
+    apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
+    apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
+                            "(level-0 MAS apply + prolongation)")
     spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, None)
     spmv_line["kernel"] = f"k_spmv_{args.spmv}"
     dominant = apply_line if kms[B.GS_K_MAS_APPLY_L0] >= kms[B.GS_K_SPMV] else spmv_line
@@ -351,6 +525,8 @@ def main():
             "pcg_iterations": iters, "true_rel_residual_last_system": true_rel,
             "l2": "inputs larger than L2 (1.07 GB of triplets and 0.6 GB of level-0 inverses per system vs 129 MB L2); no flush",
             "parallelism": f"independent systems per GPU x{world}",
+            "launch_shapes": autotune_current(B, ctx),
+            "autotune": tuned,
         },
         "roofline": dominant,
         "kernels": {"mas_apply_l0": apply_line, "spmv": spmv_line,
@@ -358,6 +534,7 @@ def main():
         "phase_ms_one_step": {B.K_NAMES[k]: float(ms_1[k]) for k in range(B.GS_K_COUNT)},
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
+        "forms": {"mixed_precision": mixed, "batched": batched},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),
@@ -382,6 +559,97 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def micro(args):
+    """The paper's microbenchmarks, one JSON line.
+
+    reduce: 2^24 3x3 blocks with sorted keys, every key repeated 2^d times;
+      the paper's FastHashReduction against the CUB library's ReduceByKey on
+      the same sorted input (both gather nothing; inputs resident in HBM).
+    spmv: random symmetric patterns, 2^18 block rows with about b blocks per
+      full row (diagonal plus (b-1)/2 random upper blocks per row); the
+      paper's symmetric storage with atomic scatter (SRBK), the row-gather
+      over the same storage, and the cuSPARSE library's BSR SpMV on the full
+      matrix; one right-hand side."""
+    import numpy as np
+    import torch
+
+    from paper_2411_06224_gb300.build import build
+
+    build()
+    from paper_2411_06224_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = B.gs_create(0, torch.cuda.current_stream())
+    gen = torch.Generator(device=dev).manual_seed(1007)
+    out = {"metric": "microbenchmarks", "config": {"workload": "paper reduction / SpMV microbenchmarks"}}
+    nb = 1 << 24
+    blocks = torch.randn((nb, 3, 3), dtype=torch.float64, device=dev, generator=gen)
+    red = []
+    for d in (0, 1, 2, 4, 7, 10, 13, 16):
+        keys = torch.arange(nb, device=dev, dtype=torch.int64) >> d
+        row = {"dup": 1 << d}
+        for method, name in ((0, "fast_hash_reduction"), (1, "cub_reduce_by_key")):
+            times = []
+            for _ in range(4):
+                o, ms = B.gs_micro_segment_reduce(ctx, keys, blocks, method)
+                times.append(ms)
+            t_ms = float(np.median(times[1:]))
+            u = o.shape[0]
+            row[name] = {"ms": t_ms, "gbs": (nb * 80 + u * 72) / t_ms / 1e6}
+        row["speedup"] = row["cub_reduce_by_key"]["ms"] / row["fast_hash_reduction"]["ms"]
+        red.append(row)
+        del keys
+    del blocks
+    out["reduce_16M_blocks"] = red
+    n = 1 << 18
+    sp = []
+    for bpr in (1, 2, 4, 8, 16, 32, 64):
+        m = (bpr - 1) / 2.0
+        k_off = int(round(m * n))
+        r_off = torch.randint(0, n - 1, (k_off,), device=dev, generator=gen)
+        span = (n - 1 - r_off).to(torch.float64)
+        c_off = r_off + 1 + (torch.rand(k_off, device=dev, generator=gen, dtype=torch.float64) * span).long()
+        rows = torch.cat([torch.arange(n, device=dev), r_off]).int()
+        cols = torch.cat([torch.arange(n, device=dev), c_off]).int()
+        vals = torch.randn((rows.numel(), 3, 3), dtype=torch.float64, device=dev, generator=gen)
+        mat = B.gs_assemble(ctx, n, rows, cols, vals)
+        _, nnzb = B.gs_mat_info(mat)
+        x = torch.randn((1, 3 * n), dtype=torch.float64, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        row = {"blocks_per_full_row": bpr, "upper_blocks": int(nnzb)}
+        for variant, name in ((B.GS_SPMV_SRBK, "srbk_symmetric"), (B.GS_SPMV_ROW, "row_gather_symmetric")):
+            B.gs_spmv(ctx, mat, x, y, nrhs=1, variant=variant)
+            B.gs_profile_begin(ctx, [B.GS_K_SPMV])
+            for _ in range(10):
+                B.gs_spmv(ctx, mat, x, y, nrhs=1, variant=variant)
+            launches, kms = B.gs_profile_end(ctx)
+            row[name] = {"ms": float(kms[B.GS_K_SPMV] / max(launches[B.GS_K_SPMV], 1))}
+        rid, cid, au = B.gs_mat_export(ctx, mat)
+        off = rid != cid
+        fr = torch.cat([rid, cid[off]]).long()
+        fc = torch.cat([cid, rid[off]]).long()
+        fa = torch.cat([au, au[off].transpose(1, 2)])
+        order = torch.argsort(fr * n + fc)
+        fr, fc, fa = fr[order], fc[order], fa[order].contiguous()
+        ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+        ptr[1:] = torch.cumsum(torch.bincount(fr, minlength=n), 0)
+        yf = torch.empty(3 * n, dtype=torch.float64, device=dev)
+        B.gs_micro_bsr_spmv_cusparse(ctx, n, ptr.int(), fc.int(), fa, x[0].contiguous(), yf, reps=2)
+        ms = B.gs_micro_bsr_spmv_cusparse(ctx, n, ptr.int(), fc.int(), fa, x[0].contiguous(), yf, reps=10)
+        row["cusparse_bsr_full"] = {"ms": ms, "full_blocks": int(fc.numel())}
+        row["max_rel_diff_vs_row_gather"] = float((yf - y[0]).abs().max() / y[0].abs().max())
+        for name in ("srbk_symmetric", "row_gather_symmetric", "cusparse_bsr_full"):
+            # algorithmic bytes of the symmetric storage: 76 B per stored block + 48 B per row
+            row[name]["gbs_symmetric_bytes"] = (nnzb * 76 + n * 48) / row[name]["ms"] / 1e6
+            row[name]["gflops"] = (2 * 9 * (2 * nnzb - n)) / row[name]["ms"] / 1e6
+        sp.append(row)
+        B.gs_mat_destroy(mat)
+    out["spmv_random_2p18_rows"] = sp
+    B.gs_destroy(ctx)
+    print(json.dumps(out), flush=True)
 
 
 def reference_arm(args, rank, world):

@@ -39,6 +39,7 @@ extern "C" {
 #define GS_ERR_MAXITER -4     /* PCG stopped at max_iter before reaching tol; x is written */
 #define GS_ERR_NONFINITE -5   /* NaN or Inf met in a reduction */
 #define GS_ERR_UNSUPPORTED -6 /* option outside the supported set (e.g. domain size > 32) */
+#define GS_ERR_TIMEOUT -7     /* a bounded wait inside a kernel gave up (no hang: the kernel returned) */
 
 typedef struct gs_ctx_s* gs_ctx;
 typedef struct gs_mat_s* gs_mat;
@@ -79,7 +80,10 @@ int gs_assemble(gs_ctx ctx, int32_t n_block_rows, const int32_t* rows, const int
 /* Two-level assembly of coupled FEM / affine-body (ABD) blocks (Sec. 5.1,
  * Sec. 5.2 "unifying four block types").
  * Inputs are 3x3 blocks in full-space node numbering (n_nodes nodes),
- * with the same row <= col convention as gs_assemble.
+ * with the same row <= col convention as gs_assemble.  An index
+ * n_nodes + 4b + a (a = 0..3) names body b's own reduced block row a: a
+ * body's 12 x 12 Hessian (inertia, orthogonality potential) enters as its
+ * 3x3 sub-blocks there (the ABD-ABD type of Sec. 5.2) with weight 1.
  * body_of_node: device int32[n_nodes], -1 for a FEM vertex, else the affine
  *   body index in [0, n_bodies).  FEM vertices must be nodes 0..n_fem-1.
  * xbar: device double[n_nodes * 3], rest coordinates of body nodes (read
@@ -89,8 +93,9 @@ int gs_assemble(gs_ctx ctx, int32_t n_block_rows, const int32_t* rows, const int
  * i.e. sub-block (a, b) = w_a(r) w_b(c) C with w = [1, xbar], and reduces
  * again.  Result block rows: FEM vertex v -> v; body b -> the four block
  * rows n_fem + 4b + {0,1,2,3} (q = [p; a_1; a_2; a_3], a_k the columns of A).
- * Errors: as gs_assemble, plus GS_ERR_INVALID for a body index out of
- * range or a body node numbered below n_fem. */
+ * Errors: as gs_assemble (indices checked against n_nodes + 4 n_bodies),
+ * plus GS_ERR_INVALID for a body index out of range or a body node
+ * numbered below n_fem. */
 int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32_t n_bodies,
                     const int32_t* body_of_node, const double* xbar, const int32_t* rows,
                     const int32_t* cols, const double* blocks, int64_t n_blocks, gs_mat* out);
@@ -128,9 +133,18 @@ int gs_spmv(gs_ctx ctx, gs_mat mat, const double* x, double* y, int32_t nrhs, in
 int gs_partition(int32_t n_nodes, const double* X, int32_t domain_size, int32_t* map,
                  int32_t* n_domains);
 
+/* Partition of several independent meshes at once (host): mesh s owns nodes
+ * [node_off[s], node_off[s+1]) and is partitioned by gs_partition on its
+ * own, its slots following those of mesh s-1, so no domain mixes meshes.
+ * node_off: host int32[n_sys + 1], node_off[0] = 0, ascending.  X, map,
+ * n_domains as gs_partition over all nodes.  Errors: GS_ERR_INVALID. */
+int gs_partition_batch(int32_t n_sys, const int32_t* node_off, const double* X, int32_t domain_size, int32_t* map,
+                       int32_t* n_domains);
+
 /* ---------------------------------------------------------------- MAS */
 #define GS_PREC_FP64 0 /* domain inverses stored and applied in FP64 */
 #define GS_PREC_FP32 1 /* inverses rounded to FP32, applied with FP32 accumulation */
+#define GS_PREC_BF16 2 /* inverses rounded to BF16 (via FP32, nearest even), FP32 accumulation */
 
 typedef struct gs_mas_opts {
   int32_t domain_size; /* N: nodes per domain, 1..32 (paper: 16 or 32, Sec. 3.2) */
@@ -201,6 +215,96 @@ int gs_mas_destroy(gs_mas mas);
 int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nrhs, double tol,
                  int32_t max_iter, int32_t spmv_variant, double* x, int32_t* iters,
                  double* rel_res);
+
+/* Mixed-precision solve: FP64 iterative refinement around an FP32 inner
+ * MAS-PCG (the paper solves in FP64 throughout; this is the library's
+ * precision form).  Each outer step recomputes r = b - A x with the FP64
+ * SpMV and stops RHS k once ||r_k|| <= tol ||b_k|| -- the true residual, so
+ * the answer meets the same test as gs_pcg_solve.  Otherwise it solves
+ * A d = r in FP32 (FP32 copy of the blocks, FP32 MAS inverses and FP32
+ * accumulation, with the p.Ap and r.z reductions and alpha, beta in FP64)
+ * until ||r_in,k|| <= inner_tol ||r_k||, and adds d to x in FP64.
+ * b, x: device double[nrhs * 3n], RHS-major as everywhere; nrhs 1..8.
+ * max_iter bounds the inner iterations summed over outer steps.
+ * iters: host int32[nrhs], inner iterations (FP32 SpMVs) per RHS; rel_res:
+ * host double[nrhs], final true residual ratio; outer_iters: host, number
+ * of refinement steps.  Any of the three may be NULL.  The FP32 copies of
+ * the blocks and inverses are made on first use and kept with the handles.
+ * Returns as gs_pcg_solve. */
+int gs_pcg_solve_mixed(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nrhs, double tol,
+                       int32_t max_iter, double inner_tol, double* x, int32_t* iters, double* rel_res,
+                       int32_t* outer_iters);
+
+/* Batched solve of independent systems, one right-hand side each (the
+ * paper solves one system at a time; this is the library's batching form).
+ * `mat` holds the systems as the diagonal blocks of one block-diagonal
+ * matrix -- system s owns block rows [node_off[s], node_off[s+1]) -- and
+ * `mas` is built on it from a gs_partition_batch map, so every SpMV and MAS
+ * apply serves all systems in one launch, while each system keeps its own
+ * PCG recurrence: its own dot products, alpha, beta and stopping test
+ * ||r_s|| <= tol ||b_s||.  use_graph != 0 runs the whole iteration loop as
+ * one CUDA graph launch (a conditional WHILE node; the loop ends when every
+ * system converged or after max_iter iterations); otherwise the host polls
+ * a convergence flag every 8 iterations.
+ * node_off: host int32[n_sys + 1]; b, x: device double[3n]; iters: host
+ * int32[n_sys]; rel_res: host double[n_sys] (either may be NULL).
+ * Returns as gs_pcg_solve. */
+int gs_pcg_solve_batch(gs_ctx ctx, gs_mat mat, gs_mas mas, int32_t n_sys, const int32_t* node_off, const double* b,
+                       double tol, int32_t max_iter, int32_t use_graph, double* x, int32_t* iters, double* rel_res);
+
+/* ---------------------------------------------------------------- adjoint */
+/* Gradients through x = A^{-1} b for a loss L(x) (the paper solves only
+ * forward; this is the library's differentiation form).
+ * x: device double[nrhs * 3n], the forward solution; g: dL/dx, same layout.
+ * lam: output dL/db = A^{-1} g, solved with the same preconditioner to tol
+ *   (mixed != 0: by gs_pcg_solve_mixed, else by gs_pcg_solve).
+ * dLdH: optional output double[nnzb * 9], the gradient with respect to each
+ *   stored block of `mat` (row-major 3x3): -sum_k (lam_r x_c^T + x_r lam_c^T)
+ *   for an off-diagonal block (it also sits transposed at (c, r)) and
+ *   -sum_k lam_r x_r^T for a diagonal block.
+ * dLdinput: optional output double[n_blocks * 9] for the triplets given to
+ *   gs_assemble: each input receives the gradient of the stored block it was
+ *   summed into, 0 for inputs below the diagonal (needs dLdH).
+ * iters: optional host int32[nrhs], iterations of the adjoint solve.
+ * Returns as gs_pcg_solve. */
+int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double* g, int32_t nrhs, double tol,
+               int32_t max_iter, int32_t mixed, double* lam, double* dLdH, double* dLdinput, int32_t* iters);
+
+/* ---------------------------------------------------------------- tuning */
+/* Launch shapes a context uses, set by the autotuner (or by hand).  Values
+ * outside the listed set return GS_ERR_INVALID.  Results do not depend on
+ * the choice except through the order of floating-point sums. */
+#define GS_TUNE_SPMV_LANES 0      /* lanes per block row of the FP64 row SpMV: 2 (default), 4, 8 */
+#define GS_TUNE_SPMV32_LANES 1    /* lanes per block row of the FP32 SpMV of the mixed solve: 2 (default), 4 */
+#define GS_TUNE_APPLY_RHS 2       /* right-hand sides per thread in the level-0 MAS product: 2, 4 (default), 8 */
+#define GS_TUNE_BATCH_CHUNK 3     /* vector entries per work item of the batched reductions: 1024..16384 (4096) */
+#define GS_TUNE_BF16_TC 4         /* BF16 level-0 apply on the tensor cores (1, default) or on FP32 cores (0);
+                                     the tensor-core form needs 3N a multiple of 16 (N = 16, 32) and nrhs <= 8 */
+int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
+int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
+
+/* ---------------------------------------------------------------- microbenchmarks */
+/* Measurement only; not part of the solve.
+ *
+ * gs_micro_segment_reduce: reduce nb 3x3 blocks (device double[nb * 9]) whose
+ * device uint64 keys are sorted ascending (each key < 2^62) into one block per
+ * distinct key, written to out (device double[nb * 9], first *n_unique used).
+ * method 0 = the paper's FastHashReduction (run flags, exclusive scan, warp
+ * head-segmented reduction; Sec. 5.2), method 1 = the CUB library's
+ * DeviceReduce::ReduceByKey, the baseline the paper compares against.
+ * *ms: device time of the reduction (events on the context's stream; for
+ * method 0 excluding the readback of the unique count between its phases).
+ *
+ * gs_micro_bsr_spmv_cusparse: y = A x with the cuSPARSE library's BSR SpMV on
+ * the FULL matrix (both triangles; 3x3 row-major blocks; device CSR-of-blocks
+ * row_ptr[n + 1], col_ind[nnzb], vals[nnzb * 9]; x, y device double[3n]),
+ * repeated `reps` times; *ms = mean time per call.  The baseline for the
+ * paper's symmetric storage (Sec. 5.3).
+ * Errors: GS_ERR_INVALID for bad arguments, GS_ERR_CUDA for library failures. */
+int gs_micro_segment_reduce(gs_ctx ctx, int64_t nb, const uint64_t* keys, const double* blocks, int32_t method,
+                            double* out, int64_t* n_unique, float* ms);
+int gs_micro_bsr_spmv_cusparse(gs_ctx ctx, int32_t n, int32_t nnzb, const int32_t* row_ptr, const int32_t* col_ind,
+                               const double* vals, const double* x, double* y, int32_t reps, float* ms);
 
 /* ---------------------------------------------------------------- measurement */
 /* Kernel classes the library counts (and optionally times) per context.

@@ -111,7 +111,10 @@ def assemble_abd(rows, cols, blocks, body_of_node, xbar, n_fem):
     4 or 1 sub-blocks (Sec. 5.2's unification), then reduce again by key.
     Inputs are taken as the full symmetric matrix's upper triangle in the
     *full-space* numbering (row <= col); node-pair blocks that map to a lower
-    body block position are transposed into the upper triangle.
+    body block position are transposed into the upper triangle.  An index
+    n_nodes + 4b + a (n_nodes = len(body_of_node)) is body b's own reduced
+    block row a: the 3x3 sub-blocks of a body's 12 x 12 Hessian (Sec. 5.2's
+    ABD-ABD block type) pass level 2 unchanged.
     """
     rid1, cid1, c1 = assemble(rows, cols, blocks)
     out_r, out_c, out_b = [], [], []
@@ -119,12 +122,18 @@ def assemble_abd(rows, cols, blocks, body_of_node, xbar, n_fem):
     for r, c, C in zip(rid1.tolist(), cid1.tolist(), c1):
         for sym in ((r, c, C),) if r == c else ((r, c, C), (c, r, C.T)):
             rr, cc, CC = sym
-            br, bc = int(body_of_node[rr]), int(body_of_node[cc])
-            if br < 0:
+            n_nodes = len(body_of_node)
+            br = int(body_of_node[rr]) if rr < n_nodes else None
+            bc = int(body_of_node[cc]) if cc < n_nodes else None
+            if br is None:
+                rows_r, w_r = [n_fem + rr - n_nodes], [1.0]
+            elif br < 0:
                 rows_r, w_r = [rr], [1.0]
             else:
                 rows_r, w_r = [n_fem + 4 * br + a for a in range(4)], abd_jacobian_weights(xbar[rr])
-            if bc < 0:
+            if bc is None:
+                rows_c, w_c = [n_fem + cc - n_nodes], [1.0]
+            elif bc < 0:
                 rows_c, w_c = [cc], [1.0]
             else:
                 rows_c, w_c = [n_fem + 4 * bc + a for a in range(4)], abd_jacobian_weights(xbar[cc])

@@ -1,0 +1,109 @@
+"""Launch-shape autotuner.
+
+Every tunable launch shape of the library (``GS_TUNE_*``) is tried on the
+caller's own matrix and preconditioner.  The kernel class that the shape
+changes is timed with the library's CUDA-event profiling
+(``gs_profile_begin``/``gs_profile_end``, events on the library's stream)
+over a few repetitions after a warm-up, and the fastest value is left set in
+the context.  Shapes change results only through the order of floating-point
+sums; a shape the problem cannot launch (too many threads per block) is
+skipped.
+
+The shapes and the kernels they steer:
+  * GS_TUNE_SPMV_LANES   lanes per block row of the FP64 row SpMV (Sec. 5.2);
+  * GS_TUNE_APPLY_RHS    right-hand sides per thread in the level-0 MAS product (Eq. 6);
+  * GS_TUNE_SPMV32_LANES lanes per block row of the FP32 SpMV inside the mixed solve;
+  * GS_TUNE_BATCH_CHUNK  vector entries per work item of the batched PCG reductions;
+  * GS_TUNE_BF16_TC      BF16 level-0 apply on the tensor cores or on the FP32 cores.
+"""
+
+import torch
+
+from . import binding as B
+
+CANDIDATES = {
+    B.GS_TUNE_SPMV_LANES: (2, 4, 8),
+    B.GS_TUNE_APPLY_RHS: (2, 4, 8),
+    B.GS_TUNE_SPMV32_LANES: (2, 4),
+    B.GS_TUNE_BATCH_CHUNK: (1024, 2048, 4096, 8192, 16384),
+    B.GS_TUNE_BF16_TC: (1, 0),
+}
+
+NAMES = {
+    B.GS_TUNE_SPMV_LANES: "spmv_lanes",
+    B.GS_TUNE_APPLY_RHS: "apply_rhs_per_thread",
+    B.GS_TUNE_SPMV32_LANES: "spmv32_lanes",
+    B.GS_TUNE_BATCH_CHUNK: "batch_chunk",
+    B.GS_TUNE_BF16_TC: "bf16_tensor_cores",
+}
+
+
+def time_class(ctx, klass, fn, reps=10, warmup=2):
+    """Mean device time (ms) of one launch of kernel class `klass` while `fn` runs."""
+    for _ in range(warmup):
+        fn()
+    B.gs_profile_begin(ctx, [klass])
+    try:
+        for _ in range(reps):
+            fn()
+    finally:
+        launches, ms = B.gs_profile_end(ctx)
+    return float(ms[klass]) / max(int(launches[klass]), 1)
+
+
+def sweep(ctx, param, klass, fn, reps=10, candidates=None):
+    """Time every candidate of `param`; leave the fastest set.  Returns (best, {value: ms})."""
+    times = {}
+    for v in candidates or CANDIDATES[param]:
+        B.gs_tune_set(ctx, param, v)
+        try:
+            times[v] = time_class(ctx, klass, fn, reps)
+        except B.GsError as e:
+            if e.status != B.GS_ERR_UNSUPPORTED:
+                raise
+    if not times:
+        raise RuntimeError(f"autotune: no launchable value for {NAMES[param]}")
+    best = min(times, key=times.get)
+    B.gs_tune_set(ctx, param, best)
+    return best, times
+
+
+def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, seed=0, bf16=False):
+    """Tune the shapes a solve on (mat, mas) with `nrhs` right-hand sides uses.
+
+    mixed:    also tune the FP32 SpMV of gs_pcg_solve_mixed;
+    bf16:     `mas` holds BF16 inverses: also choose tensor cores or FP32 cores
+              for its level-0 product;
+    node_off: block-row offsets of a batch (gs_pcg_solve_batch); tunes the
+              reduction chunk on `iters` fixed iterations.
+    Returns {name: (best value, {value: ms per launch})}.
+    """
+    n = B.gs_mat_info(mat)[0]
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.randn((nrhs, 3 * n), dtype=torch.float64, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    out = {}
+    out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(
+        ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs), reps)
+    out[NAMES[B.GS_TUNE_APPLY_RHS]] = sweep(
+        ctx, B.GS_TUNE_APPLY_RHS, B.GS_K_MAS_APPLY_L0, lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs), reps)
+    if bf16:
+        out[NAMES[B.GS_TUNE_BF16_TC]] = sweep(
+            ctx, B.GS_TUNE_BF16_TC, B.GS_K_MAS_APPLY_L0, lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs), reps)
+    if mixed:
+        out[NAMES[B.GS_TUNE_SPMV32_LANES]] = sweep(
+            ctx, B.GS_TUNE_SPMV32_LANES, B.GS_K_SPMV,
+            lambda: B.gs_pcg_solve_mixed(ctx, mat, mas, x, y.zero_(), nrhs=nrhs, tol=0.0, max_iter=iters,
+                                         raise_on_maxiter=False), max(2, reps // 5))
+    if node_off is not None:
+        b1, x1 = x[0].contiguous(), torch.empty(3 * n, dtype=torch.float64, device="cuda")
+        out[NAMES[B.GS_TUNE_BATCH_CHUNK]] = sweep(
+            ctx, B.GS_TUNE_BATCH_CHUNK, B.GS_K_PCG_VECTOR,
+            lambda: B.gs_pcg_solve_batch(ctx, mat, mas, node_off, b1, x1.zero_(), tol=0.0, max_iter=iters,
+                                         use_graph=False, raise_on_maxiter=False), max(2, reps // 5))
+    return out
+
+
+def current(ctx):
+    """The context's launch shapes as {name: value}."""
+    return {NAMES[p]: B.gs_tune_get(ctx, p) for p in CANDIDATES}

@@ -21,11 +21,13 @@ GS_ERR_NOT_SPD = -3
 GS_ERR_MAXITER = -4
 GS_ERR_NONFINITE = -5
 GS_ERR_UNSUPPORTED = -6
+GS_ERR_TIMEOUT = -7
 
 GS_SPMV_SRBK = 0
 GS_SPMV_ROW = 1
 GS_PREC_FP64 = 0
 GS_PREC_FP32 = 1
+GS_PREC_BF16 = 2
 
 # kernel classes of the profiler (supplement Eq. 1-2 cost split)
 GS_K_ASSEMBLE = 0
@@ -39,6 +41,12 @@ GS_K_MAS_APPLY_COARSE = 7
 GS_K_PCG_VECTOR = 8
 GS_K_OTHER = 9
 GS_K_COUNT = 10
+GS_TUNE_SPMV_LANES = 0
+GS_TUNE_SPMV32_LANES = 1
+GS_TUNE_APPLY_RHS = 2
+GS_TUNE_BATCH_CHUNK = 3
+GS_TUNE_BF16_TC = 4
+
 K_NAMES = ["assemble", "libprim", "spmv", "mas_levels", "mas_matrices", "mas_invert", "mas_apply_l0",
            "mas_apply_coarse", "pcg_vector", "other"]
 
@@ -56,6 +64,7 @@ EXPORTS = [
     "gs_mat_destroy",
     "gs_spmv",
     "gs_partition",
+    "gs_partition_batch",
     "gs_build_mas",
     "gs_mas_info",
     "gs_mas_export_coarse",
@@ -64,8 +73,15 @@ EXPORTS = [
     "gs_mas_apply_noalloc",
     "gs_mas_destroy",
     "gs_pcg_solve",
+    "gs_pcg_solve_mixed",
+    "gs_pcg_solve_batch",
+    "gs_adjoint",
     "gs_profile_begin",
     "gs_profile_end",
+    "gs_tune_set",
+    "gs_tune_get",
+    "gs_micro_segment_reduce",
+    "gs_micro_bsr_spmv_cusparse",
 ]
 
 
@@ -112,6 +128,7 @@ def lib():
             "gs_mat_destroy": (ctypes.c_int, [_P]),
             "gs_spmv": (ctypes.c_int, [_P, _P, _P, _P, _I32, _I32]),
             "gs_partition": (ctypes.c_int, [_I32, _P, _I32, _P, ctypes.POINTER(_I32)]),
+            "gs_partition_batch": (ctypes.c_int, [_I32, _P, _P, _I32, _P, ctypes.POINTER(_I32)]),
             "gs_build_mas": (
                 ctypes.c_int,
                 [_P, _P, _P, _I32, _P, _P, _P, _I64, ctypes.POINTER(gs_mas_opts), ctypes.POINTER(_P)],
@@ -123,7 +140,16 @@ def lib():
             "gs_mas_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
             "gs_mas_destroy": (ctypes.c_int, [_P]),
             "gs_pcg_solve": (ctypes.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _I32, _P, _P, _P]),
+            "gs_pcg_solve_mixed": (ctypes.c_int, [_P, _P, _P, _P, _I32, _D, _I32, _D, _P, _P, _P, _P]),
+            "gs_pcg_solve_batch": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _D, _I32, _I32, _P, _P, _P]),
+            "gs_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, _D, _I32, _I32, _P, _P, _P, _P]),
             "gs_profile_begin": (ctypes.c_int, [_P, ctypes.c_uint32]),
+            "gs_tune_set": (ctypes.c_int, [_P, _I32, _I32]),
+            "gs_micro_segment_reduce": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _I32, _P,
+                                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float)]),
+            "gs_micro_bsr_spmv_cusparse": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P, _P, _P, _I32,
+                                                           ctypes.POINTER(ctypes.c_float)]),
+            "gs_tune_get": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32)]),
             "gs_profile_end": (ctypes.c_int, [_P, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -253,6 +279,20 @@ def gs_partition(X, domain_size):
     return mp, nd.value
 
 
+def gs_partition_batch(X, node_off, domain_size):
+    """Host partition of several meshes (nodes [node_off[s], node_off[s+1])) -> (map, n_domains)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    off = np.ascontiguousarray(node_off, dtype=np.int32)
+    mp = np.empty(X.shape[0], dtype=np.int32)
+    nd = _I32()
+    _check(
+        lib().gs_partition_batch(off.size - 1, off.ctypes.data_as(_P), X.ctypes.data_as(_P), domain_size,
+                                 mp.ctypes.data_as(_P), ctypes.byref(nd)),
+        "gs_partition_batch",
+    )
+    return mp, nd.value
+
+
 def gs_build_mas(ctx, mat, map_, n_domains0, adj_ptr, adj, contacts, domain_size=32, max_levels=2,
                  precision=GS_PREC_FP64):
     """map_, adj_ptr, adj, contacts: int32 CUDA tensors (contacts (P, 2) or None)."""
@@ -314,6 +354,51 @@ def gs_pcg_solve(ctx, mat, mas, b, x, nrhs=1, tol=1e-6, max_iter=10_000, variant
     return iters, rel, s
 
 
+def gs_pcg_solve_mixed(ctx, mat, mas, b, x, nrhs=1, tol=1e-6, max_iter=20_000, inner_tol=1e-3,
+                       raise_on_maxiter=True):
+    """FP64 refinement around FP32 MAS-PCG; returns (inner iters, true rel_res, outer steps, status)."""
+    iters = np.zeros(nrhs, dtype=np.int32)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    outer = _I32()
+    s = lib().gs_pcg_solve_mixed(
+        ctx, mat, mas, _dev(b, torch.float64, "b"), nrhs, tol, max_iter, inner_tol, _dev(x, torch.float64, "x"),
+        iters.ctypes.data_as(_P), rel.ctypes.data_as(_P), ctypes.byref(outer),
+    )
+    if s != GS_OK and not (s == GS_ERR_MAXITER and not raise_on_maxiter):
+        raise GsError(s, "gs_pcg_solve_mixed")
+    return iters, rel, outer.value, s
+
+
+def gs_pcg_solve_batch(ctx, mat, mas, node_off, b, x, tol=1e-6, max_iter=20_000, use_graph=True,
+                       raise_on_maxiter=True):
+    """Independent PCG per system of a block-diagonal batch; returns (iters, rel_res, status)."""
+    off = np.ascontiguousarray(node_off, dtype=np.int32)
+    S = off.size - 1
+    iters = np.zeros(S, dtype=np.int32)
+    rel = np.zeros(S, dtype=np.float64)
+    s = lib().gs_pcg_solve_batch(ctx, mat, mas, S, off.ctypes.data_as(_P), _dev(b, torch.float64, "b"), tol,
+                                 max_iter, 1 if use_graph else 0, _dev(x, torch.float64, "x"),
+                                 iters.ctypes.data_as(_P), rel.ctypes.data_as(_P))
+    if s != GS_OK and not (s == GS_ERR_MAXITER and not raise_on_maxiter):
+        raise GsError(s, "gs_pcg_solve_batch")
+    return iters, rel, s
+
+
+def gs_adjoint(ctx, mat, mas, x, g, nrhs=1, tol=1e-10, max_iter=20_000, mixed=False, dLdH=None, dLdinput=None):
+    """lambda = A^{-1} g (= dL/db) plus the optional block gradients; returns (lambda, iters)."""
+    lam = torch.empty_like(g)
+    iters = np.zeros(nrhs, dtype=np.int32)
+    _check(
+        lib().gs_adjoint(
+            ctx, mat, mas, _dev(x, torch.float64, "x"), _dev(g, torch.float64, "g"), nrhs, tol, max_iter,
+            1 if mixed else 0, _dev(lam, torch.float64, "lam"), _dev(dLdH, torch.float64, "dLdH"),
+            _dev(dLdinput, torch.float64, "dLdinput"), iters.ctypes.data_as(_P),
+        ),
+        "gs_adjoint",
+    )
+    return lam, iters
+
+
 # ----------------------------------------------------------------- measurement
 def gs_profile_begin(ctx, timed_classes=()):
     mask = 0
@@ -328,3 +413,38 @@ def gs_profile_end(ctx):
     ms = np.zeros(GS_K_COUNT, dtype=np.float64)
     _check(lib().gs_profile_end(ctx, launches.ctypes.data_as(_P), ms.ctypes.data_as(_P)), "gs_profile_end")
     return launches, ms
+
+
+# ----------------------------------------------------------------- tuning
+def gs_tune_set(ctx, param, value):
+    _check(lib().gs_tune_set(ctx, param, value), "gs_tune_set")
+
+
+def gs_tune_get(ctx, param):
+    v = _I32()
+    _check(lib().gs_tune_get(ctx, param, ctypes.byref(v)), "gs_tune_get")
+    return v.value
+
+
+# ----------------------------------------------------------------- microbenchmarks
+def gs_micro_segment_reduce(ctx, keys, blocks, method):
+    """keys: sorted uint64 as int64 CUDA tensor (nb,); blocks float64 (nb, 3, 3).
+    Returns (reduced blocks (U, 3, 3), ms)."""
+    nb = keys.numel()
+    out = torch.empty((nb, 3, 3), dtype=torch.float64, device=keys.device)
+    nu = ctypes.c_int64()
+    ms = ctypes.c_float()
+    _check(lib().gs_micro_segment_reduce(ctx, nb, _dev(keys, torch.int64, "keys"), _dev(blocks, torch.float64, "blocks"),
+                                         method, _dev(out, torch.float64, "out"), ctypes.byref(nu), ctypes.byref(ms)),
+           "gs_micro_segment_reduce")
+    return out[: nu.value], ms.value
+
+
+def gs_micro_bsr_spmv_cusparse(ctx, n, row_ptr, col_ind, vals, x, y, reps=10):
+    ms = ctypes.c_float()
+    _check(lib().gs_micro_bsr_spmv_cusparse(ctx, n, col_ind.numel(), _dev(row_ptr, torch.int32, "row_ptr"),
+                                            _dev(col_ind, torch.int32, "col_ind"), _dev(vals, torch.float64, "vals"),
+                                            _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"), reps,
+                                            ctypes.byref(ms)),
+           "gs_micro_bsr_spmv_cusparse")
+    return ms.value

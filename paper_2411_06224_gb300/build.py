@@ -59,7 +59,7 @@ def build(force=False, jobs=None):
     with cf.ThreadPoolExecutor(max_workers=jobs or min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB_PATH + ".tmp"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcusparse"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

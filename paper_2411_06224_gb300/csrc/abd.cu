@@ -9,6 +9,10 @@
 // for FEM-FEM: Sec. 5.2's unification), and level 2 reduces them again.
 // Both orientations (r, c, C) and (c, r, C^T) of an off-diagonal pair are
 // expanded so that every reduced sub-block lands in the upper triangle.
+// Indices n_nodes + 4b + a name body b's own reduced block row a directly:
+// a body's 12 x 12 Hessian (inertia, orthogonality potential) enters as its
+// 16 sub-blocks, Sec. 5.2's ABD-ABD block type, and passes level 2 with
+// weight 1.
 #include <cub/device/device_scan.cuh>
 
 #include "common.cuh"
@@ -23,9 +27,15 @@ struct AbdMap {
   const double* xbar;
   int32_t n_fem;
   int32_t n_bodies;
+  int32_t n_nodes;
 };
 
 __device__ __forceinline__ int abd_targets(const AbdMap& m, int32_t node, int32_t* R, double* w) {
+  if (node >= m.n_nodes) {  // a body's own reduced block row (its 12 x 12 Hessian's 3 x 3 sub-blocks)
+    R[0] = m.n_fem + (node - m.n_nodes);
+    w[0] = 1.0;
+    return 1;
+  }
   int32_t b = m.body[node];
   if (b < 0) {
     R[0] = node;
@@ -113,13 +123,14 @@ extern "C" int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32
   GS_CHECK(n_red > 0 && n_red < (1 << 30), GS_ERR_INVALID, "gs_assemble_abd: reduced size out of range");
   GS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  AbdMap m{body_of_node, xbar, n_fem, n_bodies};
+  AbdMap m{body_of_node, xbar, n_fem, n_bodies, n_nodes};
   { GS_PROF(ctx, GS_K_OTHER); k_abd_validate<<<ceil_div(n_nodes, 256), 256, 0, st>>>(m, n_nodes, ctx->d_flags); }
   int flags = 0;
   GS_TRY(ctx->take_flags(&flags));
   if (flags) return status_from_flags(flags);
   gs_mat lvl1 = nullptr;
-  GS_TRY(gs_assemble(ctx, n_nodes, rows, cols, blocks, n_blocks, &lvl1));
+  GS_CHECK((int64_t)n_nodes + 4LL * n_bodies < (1LL << 30), GS_ERR_INVALID, "gs_assemble_abd: too many rows");
+  GS_TRY(gs_assemble(ctx, n_nodes + 4 * n_bodies, rows, cols, blocks, n_blocks, &lvl1));
   int64_t U = lvl1->nnzb;
   int32_t *cnt = nullptr, *off = nullptr, *orow = nullptr, *ocol = nullptr;
   double* oblk = nullptr;

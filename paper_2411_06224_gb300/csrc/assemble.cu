@@ -11,6 +11,7 @@
 // encoding while shortening the radix sort to 2b bits; values are gathered
 // through the sorted index instead of being sorted along (72-byte payloads
 // are read once, in the reduction).
+#include <cub/device/device_reduce.cuh>
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -48,7 +49,8 @@ __global__ void k_run_flags(const uint64_t* __restrict__ keys, int64_t nb, int32
 __global__ void k_fast_segment_reduce(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx,
                                       const int32_t* __restrict__ O, const double* __restrict__ blocks,
                                       int64_t nb, uint64_t sentinel, int shift, double* __restrict__ R,
-                                      int32_t* __restrict__ rid, int32_t* __restrict__ cid) {
+                                      int32_t* __restrict__ rid, int32_t* __restrict__ cid,
+                                      int32_t* __restrict__ key_of_input) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int lane = threadIdx.x & 31;
   bool in = i < nb;
@@ -69,6 +71,7 @@ __global__ void k_fast_segment_reduce(const uint64_t* __restrict__ keys, const u
   unsigned hm = __ballot_sync(kFull, head);
   int send = segment_end(hm, lane);
   head_segmented_reduce<9>(v, lane, send);
+  if (in) key_of_input[idx[i]] = valid ? b : -1;  // which stored block each input fed
   if (!valid) return;
   if (b_prev != b) {  // first entry of its run: record the key
     rid[b] = (int32_t)(key >> shift);
@@ -167,7 +170,9 @@ int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* col
   if (flags) return fail(status_from_flags(flags));
   m->nnzb = U;
   int s;
-  if ((s = ctx->alloc((void**)&m->au, (size_t)U * 9 * sizeof(double))) ||
+  m->n_input = nb;
+  if ((s = ctx->alloc((void**)&m->key_of_input, (size_t)std::max<int64_t>(nb, 1) * 4)) ||
+      (s = ctx->alloc((void**)&m->au, (size_t)U * 9 * sizeof(double))) ||
       (s = ctx->alloc((void**)&m->rid, (size_t)U * 4)) || (s = ctx->alloc((void**)&m->cid, (size_t)U * 4)) ||
       (s = ctx->alloc((void**)&m->row_ptr, (size_t)(n + 1) * 4)))
     return fail(s);
@@ -175,8 +180,10 @@ int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* col
     if (cudaMemsetAsync(m->au, 0, (size_t)U * 9 * sizeof(double), st) != cudaSuccess) return fail(GS_ERR_CUDA);
     const int T = 256;
     { GS_PROF(ctx, GS_K_ASSEMBLE); k_fast_segment_reduce<<<ceil_div(nb, T), T, 0, st>>>(k_out, i_out, O, blocks, nb, sentinel, shift, m->au,
-                                                            m->rid, m->cid); }
+                                                            m->rid, m->cid, m->key_of_input); }
   }
+  if (U == 0 && nb > 0 && cudaMemsetAsync(m->key_of_input, 0xff, (size_t)nb * 4, st) != cudaSuccess)
+    return fail(GS_ERR_CUDA);
   { GS_PROF(ctx, GS_K_ASSEMBLE); k_row_ptr<<<ceil_div(U + 1, 256), 256, 0, st>>>(m->rid, U, n, m->row_ptr); }
   if (cudaGetLastError() != cudaSuccess) {
     set_error("assembly kernel launch failed");
@@ -230,8 +237,121 @@ int gs_mat_destroy(gs_mat m) {
   c->release(m->lo_ptr);
   c->release(m->lo_idx);
   c->release(m->lo_col);
+  c->release(m->au32);
+  c->release(m->row_order);
+  c->release(m->key_of_input);
   delete m;
   return GS_OK;
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ measurement
+// Segmented reduction of already sorted keys, for comparing the paper's
+// FastHashReduction (run flags + exclusive scan + warp head-segmented
+// reduction, Sec. 5.2) with a library reduce-by-key on the same input.
+namespace gs {
+struct Block9 {
+  double v[9];
+};
+struct Sum9 {
+  __device__ __forceinline__ Block9 operator()(const Block9& a, const Block9& b) const {
+    Block9 c;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c.v[k] = a.v[k] + b.v[k];
+    return c;
+  }
+};
+__global__ void k_iota(uint32_t* __restrict__ a, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (uint32_t)i;
+}
+}  // namespace gs
+
+extern "C" int gs_micro_segment_reduce(gs_ctx ctx, int64_t nb, const uint64_t* keys, const double* blocks,
+                                       int32_t method, double* out, int64_t* n_unique, float* ms) {
+  using namespace gs;
+  GS_CHECK(ctx && keys && blocks && out && n_unique && ms && nb > 0 && nb < (1LL << 31), GS_ERR_INVALID,
+           "gs_micro_segment_reduce: bad argument");
+  GS_CHECK(method == 0 || method == 1, GS_ERR_INVALID, "gs_micro_segment_reduce: method %d", method);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0, e1;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  int s = GS_OK;
+  void* temp = nullptr;
+  size_t tb = 0;
+  int32_t *P = nullptr, *rid = nullptr, *cid = nullptr, *koi = nullptr;
+  uint32_t* idx = nullptr;
+  uint64_t* ukeys = nullptr;
+  int64_t* nruns = nullptr;
+  const int T = 256;
+  if (method == 0) {
+    if ((s = ctx->alloc((void**)&P, (size_t)nb * 8)) || (s = ctx->alloc((void**)&idx, (size_t)nb * 4)) ||
+        (s = ctx->alloc((void**)&rid, (size_t)nb * 4)) || (s = ctx->alloc((void**)&cid, (size_t)nb * 4)) ||
+        (s = ctx->alloc((void**)&koi, (size_t)nb * 4)))
+      goto done;
+    k_iota<<<ceil_div(nb, T), T, 0, st>>>(idx, nb);
+    int32_t* O = P + nb;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, P, O, nb, st);
+    if ((s = ctx->alloc(&temp, tb))) goto done;
+    // phase 1: flags + scan (then the unique count is read back, untimed);
+    // phase 2: zero the U outputs + segmented reduction
+    cudaEvent_t e2, e3;
+    GS_CUDA(cudaEventCreate(&e2));
+    GS_CUDA(cudaEventCreate(&e3));
+    cudaEventRecord(e0, st);
+    k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(keys, nb, P);
+    cub::DeviceScan::ExclusiveSum(temp, tb, P, O, nb, st);
+    cudaEventRecord(e1, st);
+    int32_t* ho = (int32_t*)ctx->h_pinned;
+    if (cudaMemcpyAsync(ho, O + nb - 1, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = GS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) s = GS_ERR_CUDA;
+    *n_unique = (int64_t)ho[0] + 1;
+    cudaEventRecord(e2, st);
+    cudaMemsetAsync(out, 0, (size_t)*n_unique * 72, st);
+    k_fast_segment_reduce<<<ceil_div(nb, T), T, 0, st>>>(keys, idx, O, blocks, nb, ~0ull, 32, out, rid, cid, koi);
+    cudaEventRecord(e3, st);
+    float m1 = 0.f, m2 = 0.f;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&m1, e0, e1) != cudaSuccess ||
+        cudaEventElapsedTime(&m2, e2, e3) != cudaSuccess)
+      s = GS_ERR_CUDA;
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
+    *ms = m1 + m2;
+  } else {
+    if ((s = ctx->alloc((void**)&ukeys, (size_t)nb * 8)) || (s = ctx->alloc((void**)&nruns, 8))) goto done;
+    cub::DeviceReduce::ReduceByKey(nullptr, tb, keys, ukeys, (const Block9*)blocks, (Block9*)out, nruns, Sum9(), nb,
+                                   st);
+    if ((s = ctx->alloc(&temp, tb))) goto done;
+    cudaEventRecord(e0, st);
+    cub::DeviceReduce::ReduceByKey(temp, tb, keys, ukeys, (const Block9*)blocks, (Block9*)out, nruns, Sum9(), nb,
+                                   st);
+    cudaEventRecord(e1, st);
+    int64_t* hn = (int64_t*)ctx->h_pinned;
+    if (cudaMemcpyAsync(hn, nruns, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = GS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) s = GS_ERR_CUDA;
+    *n_unique = hn[0];
+  }
+  if (s == GS_OK) {
+    if (cudaGetLastError() != cudaSuccess || (method == 1 && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)) {
+      set_error("gs_micro_segment_reduce: launch failed");
+      s = GS_ERR_CUDA;
+    }
+  } else {
+    set_error("gs_micro_segment_reduce: readback failed");
+  }
+done:
+  ctx->release(temp);
+  ctx->release(P);
+  ctx->release(idx);
+  ctx->release(rid);
+  ctx->release(cid);
+  ctx->release(koi);
+  ctx->release(ukeys);
+  ctx->release(nruns);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}

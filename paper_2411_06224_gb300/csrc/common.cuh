@@ -45,6 +45,7 @@ enum : int {
   kErrIndex = 1,      // an index out of range
   kErrNotSPD = 2,     // non-positive Cholesky pivot / p.Ap <= 0
   kErrNonFinite = 4,  // NaN / Inf in a reduction
+  kErrTimeout = 8,    // a bounded device wait gave up
 };
 
 int status_from_flags(int flags);
@@ -79,7 +80,8 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int spmv_cfg = 0;           // row-gather SpMV shape (tuning; env GS_SPMV_CFG)
+  int tune[5] = {2, 2, 4, 4096, 1};  // GS_TUNE_* launch shapes
+  cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // device error word
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
   std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls
@@ -136,6 +138,14 @@ inline int bits_for(long long n) {
 
 }  // namespace gs
 
+namespace gs {
+// Tensor-core level-0 apply (BF16 inverses); see mas_apply_tc.cu.
+bool level0_tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
+int level0_tc_prepare(gs_ctx ctx, gs_mas mas);
+int level0_tc_launch(gs_ctx ctx, gs_mas mas, bool f32_node_major, int nrhs, const void* r, int64_t stride,
+                     const void* zl, int64_t lstride, void* z, const int* skip, int* flags);
+}  // namespace gs
+
 struct gs_mat_s {
   int32_t n = 0;        // block rows
   int64_t nnzb = 0;     // stored diagonal + upper blocks
@@ -148,6 +158,10 @@ struct gs_mat_s {
   int32_t* lo_ptr = nullptr;  // n + 1
   int32_t* lo_idx = nullptr;  // nnzb - n_diag
   int32_t* lo_col = nullptr;  // the c of each such block
+  int32_t* row_order = nullptr;  // rows by descending entry count (row-gather SpMV)
+  int32_t* key_of_input = nullptr;  // per input block: index of the stored block it was summed into, -1 if dropped
+  int64_t n_input = 0;
+  float* au32 = nullptr;      // FP32 copy of au for the mixed-precision solve (built lazily)
   gs_ctx owner = nullptr;
 };
 
@@ -161,11 +175,14 @@ struct gs_mas_s {
   std::vector<int32_t*> coarse;    // per level: device int32[n] (level 0 = map)
   int32_t* remap0 = nullptr;       // device int32[n_items[0]], slot -> node or -1
   std::vector<double*> inv64;      // per level: n_domains * (3N)^2
-  std::vector<float*> inv32;       // per level (FP32 precision only)
+  std::vector<float*> inv32;       // per level (FP32 precision, or made for the mixed solve)
+  std::vector<void*> inv16;        // per level (BF16 precision only; bfloat16 entries)
+  void* inv16_tc = nullptr;        // level 0, BF16, tensor-core operand layout (BF16 precision)
   std::vector<int64_t> vec_off;    // per level l >= 1: offset (in items) into the multilevel vector
   int64_t vec_items = 0;           // total items of levels >= 1
   void** d_inv_tab = nullptr;      // device table: inverse pointer per level (FP64 or FP32)
   int32_t* d_coarse_jobs = nullptr;  // device: level then domain of every coarse-level domain
   int32_t n_coarse_jobs = 0;
+  float** d_inv32_tab = nullptr;   // device table of FP32 inverse pointers (mixed solve)
   gs_ctx owner = nullptr;
 };

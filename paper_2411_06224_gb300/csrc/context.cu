@@ -1,6 +1,5 @@
 // Context, errors and stream-ordered memory.
 #include <cstdarg>
-#include <cstdlib>
 
 #include "common.cuh"
 
@@ -27,6 +26,10 @@ int status_from_flags(int flags) {
   if (flags & kErrNonFinite) {
     set_error("non-finite value in a reduction");
     return GS_ERR_NONFINITE;
+  }
+  if (flags & kErrTimeout) {
+    set_error("a bounded wait inside a kernel gave up");
+    return GS_ERR_TIMEOUT;
   }
   return GS_OK;
 }
@@ -112,6 +115,7 @@ const char* gs_status_string(int s) {
     case GS_ERR_MAXITER: return "GS_ERR_MAXITER";
     case GS_ERR_NONFINITE: return "GS_ERR_NONFINITE";
     case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+    case GS_ERR_TIMEOUT: return "GS_ERR_TIMEOUT";
     default: return "GS_ERR_UNKNOWN";
   }
 }
@@ -135,7 +139,6 @@ int gs_create(gs_ctx* out, int device, void* stream) {
     return GS_ERR_CUDA;
   }
   c->sm_count = prop.multiProcessorCount;
-  if (const char* cfg = getenv("GS_SPMV_CFG")) c->spmv_cfg = atoi(cfg);
   // Keep freed pool memory cached by the pool instead of returning it to
   // the driver at every synchronisation.
   cudaMemPool_t pool;
@@ -186,6 +189,28 @@ int gs_profile_end(gs_ctx ctx, int64_t* launches, double* ms) {
   return GS_OK;
 }
 
+int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
+  GS_CHECK(ctx, GS_ERR_INVALID, "gs_tune_set: null context");
+  bool ok = false;
+  switch (param) {
+    case GS_TUNE_SPMV_LANES: ok = value == 2 || value == 4 || value == 8; break;
+    case GS_TUNE_SPMV32_LANES: ok = value == 2 || value == 4; break;
+    case GS_TUNE_APPLY_RHS: ok = value == 2 || value == 4 || value == 8; break;
+    case GS_TUNE_BATCH_CHUNK: ok = value >= 1024 && value <= 16384 && (value & (value - 1)) == 0; break;
+    case GS_TUNE_BF16_TC: ok = value == 0 || value == 1; break;
+    default: break;
+  }
+  GS_CHECK(ok, GS_ERR_INVALID, "gs_tune_set: value %d not allowed for parameter %d", value, param);
+  ctx->tune[param] = value;
+  return GS_OK;
+}
+
+int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value) {
+  GS_CHECK(ctx && value && param >= 0 && param < 5, GS_ERR_INVALID, "gs_tune_get: bad argument");
+  *value = ctx->tune[param];
+  return GS_OK;
+}
+
 int gs_set_stream(gs_ctx ctx, void* stream) {
   GS_CHECK(ctx != nullptr, GS_ERR_INVALID, "gs_set_stream: null context");
   ctx->stream = (cudaStream_t)stream;
@@ -199,6 +224,7 @@ int gs_destroy(gs_ctx ctx) {
   for (auto e : ctx->prof.pool) cudaEventDestroy(e);
   for (auto& b : ctx->scratch) ctx->release(b.ptr);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   cudaFree(ctx->d_flags);
   cudaFreeHost(ctx->h_pinned);
   delete ctx;

@@ -11,6 +11,10 @@
 // The dense products read each inverse once for all right-hand sides: a
 // thread owns one row of the 3N x 3N inverse and kRPT right-hand sides;
 // the inverse is symmetric, so row i is read as column i (coalesced).
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 #include "primitives.cuh"
 
@@ -23,40 +27,60 @@ struct ApplyLevels {
   int N;
 };
 
-__global__ void k_restrict(const double* __restrict__ r, int64_t stride, int nrhs, const int32_t* __restrict__ remap0,
-                           int32_t n_dom0, ApplyLevels al, double* __restrict__ rl, int64_t lstride) {
-  int32_t d = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (d >= n_dom0) return;
+// One warp per level-0 domain, four warps per block.  The 24 values (8 RHS x
+// 3) of each node go through a padded shared tile so that lane q < 24 sums
+// value q over the nodes of a group: about 31 FP64 adds per group instead
+// of the 24 x 5 of shuffle trees (FP64 adds are scarce on this part).
+// Groups are the domain's level-1 items; a level-1 item lies inside one
+// item of every coarser level, so its sums serve all levels.
+constexpr int kRestrictWarps = 4;
+
+__global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(const double* __restrict__ r, int64_t stride,
+                                                                  int nrhs, const int32_t* __restrict__ remap0,
+                                                                  int32_t n_dom0, ApplyLevels al,
+                                                                  double* __restrict__ rl, int64_t lstride) {
+  __shared__ double tile[kRestrictWarps][32][25];
+  const int wib = threadIdx.x >> 5;
+  const int32_t d = (int32_t)(blockIdx.x * kRestrictWarps + wib);
+  const int lane = threadIdx.x & 31;
+  if (d >= n_dom0) return;  // whole warp
   const int N = al.N;
-  int32_t node = lane < N ? remap0[(int64_t)d * N + lane] : -1;
+  const int32_t node = lane < N ? remap0[(int64_t)d * N + lane] : -1;
   const bool real = node >= 0;
-  for (int l = 1; l < al.L; ++l) {
-    const int32_t c = real ? al.coarse[l][node] : -1;
+  const int32_t c1 = real ? al.coarse[1][node] : -1;
+  double(*T)[25] = tile[wib];
+  for (int k0 = 0; k0 < nrhs; k0 += 8) {
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      const int k = k0 + q / 3;
+      T[lane][q] = (real && k < nrhs) ? r[k * stride + 3 * (int64_t)node + q % 3] : 0.0;
+    }
+    __syncwarp();
     uint32_t left = __ballot_sync(kFull, real);
     while (left) {
       const int lead = __ffs(left) - 1;
-      const int32_t cc = __shfl_sync(kFull, c, lead);
-      const uint32_t g = __ballot_sync(kFull, real && c == cc);
+      const int32_t cc = __shfl_sync(kFull, c1, lead);
+      const int32_t lead_node = __shfl_sync(kFull, node, lead);
+      const uint32_t g = __ballot_sync(kFull, real && c1 == cc);
       left &= ~g;
-      const bool mine = (g >> lane) & 1u;
-      for (int k = 0; k < nrhs; ++k) {
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          double v = mine ? r[k * stride + 3 * (int64_t)node + x] : 0.0;
-          v = warp_sum(v);
-          if (lane == 0) atomicAdd(&rl[k * lstride + 3 * (al.vec_off[l] + cc) + x], v);
-        }
+      if (lane < 24 && k0 + lane / 3 < nrhs) {
+        double sum = 0.0;
+        for (uint32_t m = g; m; m &= m - 1) sum += T[__ffs(m) - 1][lane];
+        const int64_t o = (k0 + lane / 3) * lstride + lane % 3;
+        atomicAdd(&rl[o + 3 * (al.vec_off[1] + cc)], sum);
+        for (int l = 2; l < al.L; ++l) atomicAdd(&rl[o + 3 * (al.vec_off[l] + al.coarse[l][lead_node])], sum);
       }
     }
+    __syncwarp();
   }
 }
 
 // Dense per-domain products.  kMode 0: coarse levels (input rl, output zl);
-// kMode 1: level 0 (gather through remap0, prolongate, write z).
-template <typename Tm, int kRPT, int kMode>
+// kMode 1: level 0 (gather through remap0, prolongate, write z).  Ts is
+// the storage type of the inverses, Tm the arithmetic type.
+template <typename Ts, typename Tm, int kRPT, int kMode>
 __global__ void __launch_bounds__(1024) k_domain_product(
-    const Tm* const* __restrict__ inv, const int32_t* __restrict__ job_level, const int32_t* __restrict__ job_dom,
+    const Ts* const* __restrict__ inv, const int32_t* __restrict__ job_level, const int32_t* __restrict__ job_dom,
     int N, int nrhs,
     // level-0 inputs / outputs
     const double* __restrict__ r, double* __restrict__ z, int64_t stride, const int32_t* __restrict__ remap0,
@@ -67,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_domain_product(
   const int ld = 3 * N;
   const int l = (kMode == 1) ? 0 : job_level[blockIdx.x];
   const int32_t d = (kMode == 1) ? blockIdx.x : job_dom[blockIdx.x];
-  const Tm* Mi = inv[l] + (int64_t)d * ld * ld;
+  const Ts* Mi = inv[l] + (int64_t)d * ld * ld;
   const int tid = threadIdx.x;
   // stage the domain's right-hand sides
   for (int e = tid; e < ld * nrhs; e += blockDim.x) {
@@ -90,7 +114,7 @@ __global__ void __launch_bounds__(1024) k_domain_product(
 #pragma unroll
   for (int q = 0; q < kRPT; ++q) acc[q] = (Tm)0;
   for (int j = 0; j < ld; ++j) {
-    const Tm m = Mi[(int64_t)j * ld + i];
+    const Tm m = (Tm)widen(Mi[(int64_t)j * ld + i]);
     const Tm* rj = sr + j * nrhs + k0;
 #pragma unroll
     for (int q = 0; q < kRPT; ++q)
@@ -120,8 +144,8 @@ __global__ void __launch_bounds__(1024) k_domain_product(
 // Coarse levels hold few domains, so each output (row i of a domain, RHS k)
 // gets its own thread: the 3N-long dot product reads row i of the symmetric
 // inverse as column i (coalesced across i) and broadcasts r.
-template <typename Tm>
-__global__ void __launch_bounds__(256) k_coarse_product(const Tm* const* __restrict__ inv,
+template <typename Ts, typename Tm>
+__global__ void __launch_bounds__(256) k_coarse_product(const Ts* const* __restrict__ inv,
                                                         const int32_t* __restrict__ job_level,
                                                         const int32_t* __restrict__ job_dom, int n_jobs, int N,
                                                         int nrhs, const double* __restrict__ rl,
@@ -135,15 +159,15 @@ __global__ void __launch_bounds__(256) k_coarse_product(const Tm* const* __restr
   const int k = rem / ld, i = rem % ld;
   const int l = job_level[job];
   const int32_t d = job_dom[job];
-  const Tm* Mi = inv[l] + (int64_t)d * ld * ld;
+  const Ts* Mi = inv[l] + (int64_t)d * ld * ld;
   const double* rj = rl + k * lstride + 3 * (al.vec_off[l] + (int64_t)d * N);
   Tm acc = (Tm)0;
-  for (int j = 0; j < ld; ++j) acc += Mi[(int64_t)j * ld + i] * (Tm)rj[j];
+  for (int j = 0; j < ld; ++j) acc += (Tm)widen(Mi[(int64_t)j * ld + i]) * (Tm)rj[j];
   zl[k * lstride + 3 * (al.vec_off[l] + (int64_t)d * N) + i] = (double)acc;
 }
 
-template <typename Tm>
-static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const int32_t* d_jobs, int n_coarse_jobs,
+template <typename Ts, typename Tm>
+static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const int32_t* d_jobs, int n_coarse_jobs,
                         const double* r, double* z, int nrhs, double* rl, double* zl) {
   cudaStream_t st = ctx->stream;
   const int N = mas->N, ld = 3 * N;
@@ -156,34 +180,49 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Tm* const* d_inv, const in
     al.coarse[l] = mas->coarse[l];
     al.vec_off[l] = mas->vec_off[l];
   }
-  constexpr int kRPT = 4;
+  const int kRPT = ctx->tune[GS_TUNE_APPLY_RHS];
   const int groups = ceil_div(nrhs, kRPT);
   const int threads = ((ld * groups + 31) / 32) * 32;
   const size_t smem = (size_t)ld * nrhs * sizeof(Tm);
   GS_CHECK(threads <= 1024, GS_ERR_UNSUPPORTED, "mas apply: too many right-hand sides (%d)", nrhs);
   if (mas->L > 1) {
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
-    { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(r, stride, nrhs, mas->remap0,
+    { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div(mas->n_domains[0], kRestrictWarps), 32 * kRestrictWarps, 0, st>>>(r, stride, nrhs, mas->remap0,
                                                                               mas->n_domains[0], al, rl, lstride); }
     {
       GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
       const int64_t outs = (int64_t)n_coarse_jobs * ld * nrhs;
-      k_coarse_product<Tm><<<ceil_div(outs, 256), 256, 0, st>>>(d_inv, d_jobs, d_jobs + n_coarse_jobs, n_coarse_jobs,
+      k_coarse_product<Ts, Tm><<<ceil_div(outs, 256), 256, 0, st>>>(d_inv, d_jobs, d_jobs + n_coarse_jobs, n_coarse_jobs,
                                                                 N, nrhs, rl, zl, lstride, al);
     }
   }
-  { GS_PROF(ctx, GS_K_MAS_APPLY_L0); k_domain_product<Tm, kRPT, 1><<<mas->n_domains[0], threads, smem, st>>>(d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride,
-                                                                         mas->remap0, rl, zl, lstride, al); }
+  if (std::is_same<Ts, __nv_bfloat16>::value && level0_tc_usable(ctx, mas, nrhs)) {
+    GS_PROF(ctx, GS_K_MAS_APPLY_L0);
+    GS_TRY(level0_tc_launch(ctx, mas, false, nrhs, r, stride, zl, lstride, z, nullptr, ctx->d_flags));
+  } else {
+    GS_PROF(ctx, GS_K_MAS_APPLY_L0);
+#define GS_L0_ARGS d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al
+    if (kRPT == 2)
+      k_domain_product<Ts, Tm, 2, 1><<<mas->n_domains[0], threads, smem, st>>>(GS_L0_ARGS);
+    else if (kRPT == 8)
+      k_domain_product<Ts, Tm, 8, 1><<<mas->n_domains[0], threads, smem, st>>>(GS_L0_ARGS);
+    else
+      k_domain_product<Ts, Tm, 4, 1><<<mas->n_domains[0], threads, smem, st>>>(GS_L0_ARGS);
+#undef GS_L0_ARGS
+  }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
 
 int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl) {
+  if (mas->precision == GS_PREC_BF16)
+    return launch_apply<__nv_bfloat16, float>(ctx, mas, (const __nv_bfloat16* const*)mas->d_inv_tab,
+                                              mas->d_coarse_jobs, mas->n_coarse_jobs, r, z, nrhs, rl, zl);
   if (mas->precision == GS_PREC_FP32)
-    return launch_apply<float>(ctx, mas, (const float* const*)mas->d_inv_tab, mas->d_coarse_jobs,
-                               mas->n_coarse_jobs, r, z, nrhs, rl, zl);
-  return launch_apply<double>(ctx, mas, (const double* const*)mas->d_inv_tab, mas->d_coarse_jobs,
-                              mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+    return launch_apply<float, float>(ctx, mas, (const float* const*)mas->d_inv_tab, mas->d_coarse_jobs,
+                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+  return launch_apply<double, double>(ctx, mas, (const double* const*)mas->d_inv_tab, mas->d_coarse_jobs,
+                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl);
 }
 
 int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl) {
@@ -203,5 +242,11 @@ extern "C" int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, 
   GS_CUDA(cudaSetDevice(ctx->device));
   double *rl, *zl;
   GS_TRY(gs::mas_level_vectors(ctx, mas, nrhs, &rl, &zl));
-  return gs::mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl);
+  GS_TRY(gs::mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
+  if (gs::level0_tc_usable(ctx, mas, nrhs)) {  // the tensor-core kernel reports bounded-wait timeouts
+    int flags = 0;
+    GS_TRY(ctx->take_flags(&flags));
+    if (flags) return gs::status_from_flags(flags);
+  }
+  return GS_OK;
 }

@@ -23,6 +23,7 @@
 // the real items' part in shared memory (Cholesky, FP64), inverts the
 // factor and forms L^-T L^-1, overwriting the matrix with its inverse.
 #include <cub/device/device_scan.cuh>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "primitives.cuh"
@@ -357,6 +358,12 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
   if (i < n) b[i] = (float)a[i];
 }
 
+// double -> float -> bfloat16, both roundings to nearest even
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -369,9 +376,12 @@ int gs_mas_destroy(gs_mas mas) {
   for (auto p : mas->coarse) c->release(p);
   for (auto p : mas->inv64) c->release(p);
   for (auto p : mas->inv32) c->release(p);
+  for (auto p : mas->inv16) c->release(p);
+  c->release(mas->inv16_tc);
   c->release(mas->remap0);
   c->release(mas->d_inv_tab);
   c->release(mas->d_coarse_jobs);
+  c->release(mas->d_inv32_tab);
   delete mas;
   return GS_OK;
 }
@@ -386,7 +396,8 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   GS_CHECK(N <= 32, GS_ERR_UNSUPPORTED, "gs_build_mas: domain_size %d > 32", N);
   GS_CHECK(opts->max_levels >= 1 && opts->max_levels <= 8, GS_ERR_INVALID, "gs_build_mas: max_levels %d",
            opts->max_levels);
-  GS_CHECK(opts->precision == GS_PREC_FP64 || opts->precision == GS_PREC_FP32, GS_ERR_INVALID,
+  GS_CHECK(opts->precision == GS_PREC_FP64 || opts->precision == GS_PREC_FP32 || opts->precision == GS_PREC_BF16,
+           GS_ERR_INVALID,
            "gs_build_mas: precision %d", opts->precision);
   const int32_t n = mat->n;
   GS_CHECK(map && adj_ptr && (adj || true), GS_ERR_INVALID, "gs_build_mas: null map or graph");
@@ -517,6 +528,16 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     return fail(GS_ERR_CUDA);
   { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
                                             ctx->d_flags); }
+  if (opts->precision == GS_PREC_BF16) {
+    for (int l = 0; l < L; ++l) {
+      void* f = nullptr;
+      int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
+      if ((s = ctx->alloc(&f, (size_t)cnt * 2))) return fail(s);
+      mas->inv16.push_back(f);
+      { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_bf16<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], (__nv_bfloat16*)f, cnt); }
+    }
+    if ((s = level0_tc_prepare(ctx, mas))) return fail(s);
+  }
   if (opts->precision == GS_PREC_FP32) {
     for (int l = 0; l < L; ++l) {
       float* f = nullptr;
@@ -538,7 +559,9 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   {
     std::vector<void*> hp(8, nullptr);
     for (int l = 0; l < L; ++l)
-      hp[l] = opts->precision == GS_PREC_FP32 ? (void*)mas->inv32[l] : (void*)mas->inv64[l];
+      hp[l] = opts->precision == GS_PREC_FP32   ? (void*)mas->inv32[l]
+              : opts->precision == GS_PREC_BF16 ? mas->inv16[l]
+                                                : (void*)mas->inv64[l];
     std::vector<int32_t> lev, dom;
     for (int l = 1; l < L; ++l)
       for (int32_t d = 0; d < mas->n_domains[l]; ++d) lev.push_back(l), dom.push_back(d);

@@ -85,3 +85,30 @@ extern "C" int gs_partition(int32_t n, const double* X, int32_t N, int32_t* map,
   *n_domains = b.next;
   return GS_OK;
 }
+
+// Several independent meshes, each partitioned on its own (no domain mixes
+// two meshes): mesh s owns nodes [node_off[s], node_off[s+1]) and its parts
+// follow those of mesh s-1.
+extern "C" int gs_partition_batch(int32_t n_sys, const int32_t* node_off, const double* X, int32_t N, int32_t* map,
+                                  int32_t* n_domains) {
+  if (n_sys < 1 || !node_off || !X || !map || !n_domains || N < 1 || node_off[0] != 0) {
+    gs::set_error("gs_partition_batch: bad argument");
+    return GS_ERR_INVALID;
+  }
+  int32_t dom = 0;
+  for (int32_t s = 0; s < n_sys; ++s) {
+    const int32_t b = node_off[s], e = node_off[s + 1];
+    if (e < b) {
+      gs::set_error("gs_partition_batch: offsets not ascending");
+      return GS_ERR_INVALID;
+    }
+    if (e == b) continue;
+    int32_t nd = 0;
+    int st = gs_partition(e - b, X + 3 * (int64_t)b, N, map + b, &nd);
+    if (st != GS_OK) return st;
+    for (int32_t v = b; v < e; ++v) map[v] += dom * N;
+    dom += nd;
+  }
+  *n_domains = dom;
+  return GS_OK;
+}

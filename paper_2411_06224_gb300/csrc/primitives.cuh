@@ -1,6 +1,7 @@
 // Warp-level building blocks.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,11 @@ __device__ __forceinline__ void head_segmented_reduce(double (&v)[K], int lane, 
     }
   }
 }
+
+// Stored inverse entry -> arithmetic type (FP64, FP32 or BF16 storage).
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

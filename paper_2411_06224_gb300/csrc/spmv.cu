@@ -76,16 +76,20 @@ __global__ void __launch_bounds__(256) k_spmv_srbk(const int32_t* __restrict__ r
 // (its upper blocks first, then its transposed references) and keeps kR
 // right-hand sides in registers, so every block is loaded once per kR RHS.
 template <int kLanes, int kR>
-__global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
+__global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_order,
+                                                  const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
                                                   const int32_t* __restrict__ lo_ptr,
                                                   const int32_t* __restrict__ lo_idx,
                                                   const int32_t* __restrict__ lo_col, const double* __restrict__ au,
                                                   int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
                                                   double* __restrict__ y) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t row = (int32_t)(t / kLanes);
+  const int32_t slot = (int32_t)(t / kLanes);
   int sub = threadIdx.x % kLanes;
-  bool in = row < n;
+  bool in = slot < n;
+  // rows are taken longest first (stable), so the rows sharing a warp have
+  // equal lengths and no lane idles while the FP64 pipe issues for the warp
+  const int32_t row = in ? row_order[slot] : 0;
   int32_t u0 = 0, u1 = 0, l0 = 0, l1 = 0;
   if (in) {
     u0 = row_ptr[row], u1 = row_ptr[row + 1];
@@ -169,6 +173,17 @@ __global__ void k_lower_fill(const uint32_t* __restrict__ skey, const uint32_t* 
   }
 }
 
+// Sort key of each row for the row order: entries counted from the longest
+// possible, so an ascending radix sort lists long rows first.
+__global__ void k_row_len_keys(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ lo_ptr, int32_t n,
+                               uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+  int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t len = (uint32_t)(row_ptr[r + 1] - row_ptr[r] + lo_ptr[r + 1] - lo_ptr[r]);
+  key[r] = 0xffffffffu - len;
+  val[r] = (uint32_t)r;
+}
+
 // Number of valid (non-sentinel) keys in a sorted key array.
 __global__ void k_count_valid(const uint32_t* __restrict__ k, int64_t nz, int32_t* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,6 +226,21 @@ int ensure_lower(gs_ctx ctx, gs_mat m) {
   { GS_PROF(ctx, GS_K_OTHER); k_lower_fill<<<ceil_div(n_off + 1, 256), 256, 0, st>>>(k_out, v_out, m->rid, n_off, m->n, m->lo_ptr, m->lo_idx,
                                                          m->lo_col); }
   GS_CUDA(cudaGetLastError());
+  // row order: by total entries, longest first, ties by row index
+  GS_TRY(ctx->alloc((void**)&m->row_order, (size_t)std::max(m->n, 1) * 4));
+  {
+    uint32_t *lk_in, *lk_out, *lv_in;
+    GS_TRY(ctx->scratch_buf(kSlotSortKeysIn, (size_t)m->n * 4 + 16, (void**)&lk_in));
+    GS_TRY(ctx->scratch_buf(kSlotSortKeysOut, (size_t)m->n * 4 + 16, (void**)&lk_out));
+    GS_TRY(ctx->scratch_buf(kSlotSortValsIn, (size_t)m->n * 4 + 16, (void**)&lv_in));
+    { GS_PROF(ctx, GS_K_OTHER); k_row_len_keys<<<ceil_div(m->n, 256), 256, 0, st>>>(m->row_ptr, m->lo_ptr, m->n, lk_in, lv_in); }
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, lk_in, lk_out, lv_in, (uint32_t*)m->row_order, m->n, 0, 32, st);
+    void* temp;
+    GS_TRY(ctx->scratch_buf(kSlotSortTemp, tb, &temp));
+    { GS_PROF(ctx, GS_K_LIBPRIM); GS_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, lk_in, lk_out, lv_in, (uint32_t*)m->row_order, m->n, 0, 32, st)); }
+  }
+  GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
 
@@ -224,12 +254,11 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
       { GS_PROF(ctx, GS_K_SPMV); k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y); }
   } else {
     GS_TRY(ensure_lower(ctx, m));
-    // lanes per row x RHS per pass (ctx->spmv_cfg: 0 = 2x8, 1 = 8x4, 2 = 4x8)
-    const int cfg = ctx->spmv_cfg;
-    const int lanes = cfg == 1 ? 8 : (cfg == 2 ? 4 : 2);
+    // lanes per block row (GS_TUNE_SPMV_LANES); 8 lanes keep 4 RHS per pass
+    const int lanes = ctx->tune[GS_TUNE_SPMV_LANES];
     const int64_t threads = (int64_t)m->n * lanes;
     const int grid = ceil_div(threads, 256);
-#define GS_ROW_ARGS m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col, m->au, m->n, stride, nrhs, x, y
+#define GS_ROW_ARGS m->row_order, m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col, m->au, m->n, stride, nrhs, x, y
     if (nrhs == 1) {
       if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }

@@ -79,3 +79,9 @@ def test_partition_rejects_bad_input(B):
     assert e.value.status == B.GS_ERR_INVALID
     with pytest.raises(B.GsError):
         B.gs_partition(np.zeros((4, 3)), 0)
+
+
+def test_tune_entry_points_reject_a_null_context(B):
+    v = ctypes.c_int32(0)
+    assert B.lib().gs_tune_set(None, B.GS_TUNE_SPMV_LANES, 2) == B.GS_ERR_INVALID
+    assert B.lib().gs_tune_get(None, B.GS_TUNE_SPMV_LANES, ctypes.byref(v)) == B.GS_ERR_INVALID

@@ -134,8 +134,9 @@ def test_abd_two_level_matches_oracle(B, ctx):
     body = np.array([-1] * n_fem + [b for b in range(n_bodies) for _ in range(per)], dtype=np.int32)
     xbar = rng.normal(size=(n_full, 3))
     K = 3000
-    rows = rng.integers(0, n_full, K).astype(np.int32)
-    cols = rng.integers(0, n_full, K).astype(np.int32)
+    # node indices, plus the bodies' own reduced rows n_full + 4b + a (12 x 12 body Hessians)
+    rows = rng.integers(0, n_full + 4 * n_bodies, K).astype(np.int32)
+    cols = rng.integers(0, n_full + 4 * n_bodies, K).astype(np.int32)
     lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
     blocks = rng.normal(size=(K, 3, 3))
     mat = B.gs_assemble_abd(ctx, n_full, n_fem, n_bodies, dev(body, torch.int32), dev(xbar, torch.float64),

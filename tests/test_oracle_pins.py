@@ -106,6 +106,38 @@ def test_abd_two_level_equals_dense_jacobian_product():
     np.testing.assert_allclose(got, J.T @ A @ J, rtol=1e-12, atol=1e-12)
 
 
+def test_abd_body_rows_take_a_bodys_own_hessian_unchanged():
+    # Sec. 5.2: a 12 x 12 ABD-ABD block is 16 sub-blocks on the body's reduced
+    # rows; given at indices n_full + 4b + a they add to J^T A J as they are.
+    rng = np.random.default_rng(12)
+    n_full, n_fem, n_bodies = 9, 3, 2
+    body = np.array([-1] * n_fem + [0, 0, 0, 1, 1, 1])
+    xbar = rng.normal(size=(n_full, 3))
+    K = 60
+    rows, cols = rng.integers(0, n_full, K), rng.integers(0, n_full, K)
+    lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
+    blocks = rng.normal(size=(K, 3, 3))
+    H = [rng.normal(size=(12, 12)) for _ in range(n_bodies)]
+    H = [h + h.T for h in H]
+    br, bc, bb = [], [], []
+    for b in range(n_bodies):
+        for a in range(4):
+            for c in range(a, 4):
+                br.append(n_full + 4 * b + a)
+                bc.append(n_full + 4 * b + c)
+                bb.append(H[b][3 * a : 3 * a + 3, 3 * c : 3 * c + 3])
+    rid, cid, au = assembly.assemble_abd(np.concatenate([lo, br]), np.concatenate([hi, bc]),
+                                         np.concatenate([blocks, np.array(bb)]), body, xbar, n_fem)
+    n_red = n_fem + 4 * n_bodies
+    got = assembly.to_dense(n_red, rid, cid, au)
+    r1, c1, a1 = assembly.assemble_abd(lo, hi, blocks, body, xbar, n_fem)
+    want = assembly.to_dense(n_red, r1, c1, a1)
+    for b in range(n_bodies):
+        s = 3 * (n_fem + 4 * b)
+        want[s : s + 12, s : s + 12] += H[b]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
 # ---------------------------------------------------------------- SpMV (Sec. 5.3)
 
 
