@@ -36,6 +36,9 @@ FP64_FMA_PER_CLK_PER_SM = 2  # GB300: derived from the nominal 1.25 TFLOP/s FP64
 # ncu capture on the 40^3 case (profiles/k_domain_product_fp64_tet40.md):
 # 172.9 MB over 2000 domains; traffic grows with the domain count.
 APPLY_DRAM_BYTES_PER_DOMAIN_8RHS = 172.9e6 / 2000
+# DRAM bytes per level-0 domain of the digit-split tensor-core apply at 8 RHS,
+# from an ncu capture (set once measured; None until then)
+F64TC_DRAM_BYTES_PER_DOMAIN_8RHS = None
 TOL = 1e-6
 METRIC = "Newton solves/s to 1e-6 rel. residual (FP64 MAS-PCG)"
 
@@ -242,7 +245,8 @@ def main():
         mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
         mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
                              domain_size=N, max_levels=L, precision=prec)
-        res = autotune.tune(ctx, mat, mas, nrhs=args.nrhs, reps=5, mixed=args.mixed_steps > 0)
+        res = autotune.tune(ctx, mat, mas, nrhs=args.nrhs, reps=5, mixed=args.mixed_steps > 0,
+                            fp64=prec == B.GS_PREC_FP64)
         B.gs_mas_destroy(mas)
         if args.mixed_steps > 0 and args.nrhs <= 8:  # BF16 level-0 product: tensor cores or FP32 cores
             mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
@@ -333,7 +337,7 @@ def main():
 
     # the mixed-precision forms on the same workload and right-hand sides:
     #   f64_pcg_f32_mas   FP64 PCG, MAS inverses stored and applied in FP32
-    #   f64_pcg_bf16_mas  FP64 PCG, BF16 inverses, level-0 product on the tensor cores
+    #   f64_pcg_bf16_mas  FP64 PCG, BF16 level-0 inverse Cholesky factors on the tensor cores
     #   f32_inner_pcg     FP32 PCG (FP32 SpMV + FP32 MAS) with FP64 reliable updates
     mixed = None
     if args.mixed_steps > 0 and args.nrhs <= 8:
@@ -493,12 +497,30 @@ def main():
                 "hbm_gbs": nbytes / tsec / 1e9, "hbm_frac": nbytes / tsec / 1e9 / hbm,
                 "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
 
-    traffic = (APPLY_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
-               if args.nrhs == 8 and prec == B.GS_PREC_FP64 and N == 32
-               and B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS) == 4 else None)  # the captured shape
-    apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
-    apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
-                            "(level-0 MAS apply + prolongation)")
+    f64tc = (prec == B.GS_PREC_FP64 and args.nrhs <= 8 and ld % 16 == 0
+             and B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 1)
+    if f64tc:
+        # FP64-accurate apply on the BF16 tensor cores: the 7 BF16 digit matrices
+        # of every level-0 inverse (14 B per entry) stream from HBM once per apply,
+        # plus r read and z written (FP64), plus the coarse z read once per node
+        dig_bytes = 7 * 2 * n_dom0 * ld * ld
+        tc_bytes = dig_bytes + 2 * 8 * 3 * V * args.nrhs
+        traffic = (F64TC_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
+                   if args.nrhs == 8 and N == 32 and F64TC_DRAM_BYTES_PER_DOMAIN_8RHS else None)
+        apply_line = {"bound": "hbm", "achieved": tc_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": tc_bytes / t_apply / 1e9 / hbm, "traffic": traffic,
+                      "fp64_equivalent_tflops": apply_flops / t_apply / 1e12,
+                      "fp64_equivalent_frac_of_fp64_peak": apply_flops / t_apply / 1e12 / fp64_peak_tflops,
+                      "flops_per_launch": apply_flops, "bytes_per_launch": tc_bytes, "avg_launch_ms": t_apply * 1e3,
+                      "kernel": "k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
+                                "splitting on tcgen05, + prolongation)"}
+    else:
+        traffic = (APPLY_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
+                   if args.nrhs == 8 and prec == B.GS_PREC_FP64 and N == 32
+                   and B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS) == 4 else None)  # the captured shape
+        apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
+        apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
+                                "(level-0 MAS apply + prolongation)")
     spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, None)
     spmv_line["kernel"] = f"k_spmv_{args.spmv}"
     dominant = apply_line if kms[B.GS_K_MAS_APPLY_L0] >= kms[B.GS_K_SPMV] else spmv_line

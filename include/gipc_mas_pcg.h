@@ -144,7 +144,11 @@ int gs_partition_batch(int32_t n_sys, const int32_t* node_off, const double* X, 
 /* ---------------------------------------------------------------- MAS */
 #define GS_PREC_FP64 0 /* domain inverses stored and applied in FP64 */
 #define GS_PREC_FP32 1 /* inverses rounded to FP32, applied with FP32 accumulation */
-#define GS_PREC_BF16 2 /* inverses rounded to BF16 (via FP32, nearest even), FP32 accumulation */
+#define GS_PREC_BF16 2 /* level 0: the inverse Cholesky factor W (M_d^-1 = W^T W) rounded to BF16
+                          (via FP32, nearest even), applied as W^T (W r) with FP32 accumulation, on
+                          the tensor cores when 3N is a multiple of 16 and nrhs <= 8; coarse levels
+                          as GS_PREC_FP32.  Rounding the factor, not the inverse, keeps the
+                          preconditioner positive semi-definite. */
 
 typedef struct gs_mas_opts {
   int32_t domain_size; /* N: nodes per domain, 1..32 (paper: 16 or 32, Sec. 3.2) */
@@ -216,19 +220,21 @@ int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nr
                  int32_t max_iter, int32_t spmv_variant, double* x, int32_t* iters,
                  double* rel_res);
 
-/* Mixed-precision solve: FP64 iterative refinement around an FP32 inner
- * MAS-PCG (the paper solves in FP64 throughout; this is the library's
- * precision form).  Each outer step recomputes r = b - A x with the FP64
- * SpMV and stops RHS k once ||r_k|| <= tol ||b_k|| -- the true residual, so
- * the answer meets the same test as gs_pcg_solve.  Otherwise it solves
- * A d = r in FP32 (FP32 copy of the blocks, FP32 MAS inverses and FP32
- * accumulation, with the p.Ap and r.z reductions and alpha, beta in FP64)
- * until ||r_in,k|| <= inner_tol ||r_k||, and adds d to x in FP64.
+/* Mixed-precision solve: one FP32 MAS-PCG recurrence with FP64 reliable
+ * updates (the paper solves in FP64 throughout; this is the library's
+ * precision form).  The recurrence runs on an FP32 copy of the blocks, the
+ * FP32 (or, for a GS_PREC_BF16 MAS, the BF16-factored) preconditioner and
+ * FP32 vectors, with the p.Ap and r.z reductions and alpha, beta in FP64.
+ * Once RHS k's FP32 residual has fallen by inner_tol since its last
+ * correction, x_k += d_k in FP64, r_k = b_k - A x_k is recomputed with the
+ * FP64 SpMV and the recurrence continues from it (search direction kept).
+ * RHS k stops once that true residual satisfies ||r_k|| <= tol ||b_k||, the
+ * same test as gs_pcg_solve.
  * b, x: device double[nrhs * 3n], RHS-major as everywhere; nrhs 1..8.
  * max_iter bounds the inner iterations summed over outer steps.
  * iters: host int32[nrhs], inner iterations (FP32 SpMVs) per RHS; rel_res:
  * host double[nrhs], final true residual ratio; outer_iters: host, number
- * of refinement steps.  Any of the three may be NULL.  The FP32 copies of
+ * of reliable updates.  Any of the three may be NULL.  The FP32 copies of
  * the blocks and inverses are made on first use and kept with the handles.
  * Returns as gs_pcg_solve. */
 int gs_pcg_solve_mixed(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int32_t nrhs, double tol,
@@ -280,6 +286,9 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 #define GS_TUNE_BATCH_CHUNK 3     /* vector entries per work item of the batched reductions: 1024..16384 (4096) */
 #define GS_TUNE_BF16_TC 4         /* BF16 level-0 apply on the tensor cores (1, default) or on FP32 cores (0);
                                      the tensor-core form needs 3N a multiple of 16 (N = 16, 32) and nrhs <= 8 */
+#define GS_TUNE_F64_TC 5          /* FP64 level-0 apply on the BF16 tensor cores by exact digit splitting (1,
+                                     default; FP64 accuracy) or on the FP64 cores (0); needs 3N a multiple
+                                     of 16 and nrhs <= 8 */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
 

@@ -183,6 +183,28 @@ def invert_domains(lv, mats):
     return invs
 
 
+def inverse_factors(lv, mats):
+    """Per-domain inverse Cholesky factors W = L^{-1} (lower triangular) of the
+    real items' part, M_d = L L^T, so that M_d^{-1} = W^T W; padded rows and
+    columns zero.  The low-precision (BF16) preconditioner stores W instead of
+    M_d^{-1}: any rounding of W keeps W^T W positive semi-definite."""
+    N = lv.N
+    facs = []
+    for l, Ms in enumerate(mats):
+        real = np.zeros(lv.n_domains(l) * N, dtype=bool)
+        real[: lv.n_items[l]] = lv.real[l]
+        fac = np.zeros_like(Ms)
+        for d in range(Ms.shape[0]):
+            lanes = np.nonzero(real[d * N : d * N + N])[0]
+            if lanes.size == 0:
+                continue
+            idx = (3 * lanes[:, None] + np.arange(3)[None]).ravel()
+            L = np.linalg.cholesky(Ms[d][np.ix_(idx, idx)])
+            fac[d][np.ix_(idx, idx)] = np.linalg.inv(L)
+        facs.append(fac)
+    return facs
+
+
 def coarsener(lv, l):
     """C_l of supplement Eq. 5-6 as a sparse 0/1 matrix acting on nodes:
     row a (an item of level l, padded domains included) sums the nodes u with

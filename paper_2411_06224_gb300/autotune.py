@@ -14,7 +14,9 @@ The shapes and the kernels they steer:
   * GS_TUNE_APPLY_RHS    right-hand sides per thread in the level-0 MAS product (Eq. 6);
   * GS_TUNE_SPMV32_LANES lanes per block row of the FP32 SpMV inside the mixed solve;
   * GS_TUNE_BATCH_CHUNK  vector entries per work item of the batched PCG reductions;
-  * GS_TUNE_BF16_TC      BF16 level-0 apply on the tensor cores or on the FP32 cores.
+  * GS_TUNE_BF16_TC      BF16 level-0 apply on the tensor cores or on the FP32 cores;
+  * GS_TUNE_F64_TC       FP64 level-0 apply on the BF16 tensor cores (exact digit
+                         splitting) or on the FP64 cores.
 """
 
 import torch
@@ -27,6 +29,7 @@ CANDIDATES = {
     B.GS_TUNE_SPMV32_LANES: (2, 4),
     B.GS_TUNE_BATCH_CHUNK: (1024, 2048, 4096, 8192, 16384),
     B.GS_TUNE_BF16_TC: (1, 0),
+    B.GS_TUNE_F64_TC: (1, 0),
 }
 
 NAMES = {
@@ -35,6 +38,7 @@ NAMES = {
     B.GS_TUNE_SPMV32_LANES: "spmv32_lanes",
     B.GS_TUNE_BATCH_CHUNK: "batch_chunk",
     B.GS_TUNE_BF16_TC: "bf16_tensor_cores",
+    B.GS_TUNE_F64_TC: "fp64_on_tensor_cores",
 }
 
 
@@ -68,12 +72,14 @@ def sweep(ctx, param, klass, fn, reps=10, candidates=None):
     return best, times
 
 
-def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, seed=0, bf16=False):
+def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, seed=0, bf16=False, fp64=False):
     """Tune the shapes a solve on (mat, mas) with `nrhs` right-hand sides uses.
 
     mixed:    also tune the FP32 SpMV of gs_pcg_solve_mixed;
-    bf16:     `mas` holds BF16 inverses: also choose tensor cores or FP32 cores
+    bf16:     `mas` holds BF16 factors: also choose tensor cores or FP32 cores
               for its level-0 product;
+    fp64:     `mas` is FP64: also choose the digit-split tensor-core product or
+              the FP64-core product for level 0;
     node_off: block-row offsets of a batch (gs_pcg_solve_batch); tunes the
               reduction chunk on `iters` fixed iterations.
     Returns {name: (best value, {value: ms per launch})}.
@@ -85,8 +91,11 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     out = {}
     out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(
         ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs), reps)
-    out[NAMES[B.GS_TUNE_APPLY_RHS]] = sweep(
-        ctx, B.GS_TUNE_APPLY_RHS, B.GS_K_MAS_APPLY_L0, lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs), reps)
+    apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
+    if fp64:
+        out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps)
+    if not fp64 or B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 0:  # the FP64-core kernel's shape
+        out[NAMES[B.GS_TUNE_APPLY_RHS]] = sweep(ctx, B.GS_TUNE_APPLY_RHS, B.GS_K_MAS_APPLY_L0, apply, reps)
     if bf16:
         out[NAMES[B.GS_TUNE_BF16_TC]] = sweep(
             ctx, B.GS_TUNE_BF16_TC, B.GS_K_MAS_APPLY_L0, lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs), reps)

@@ -80,7 +80,7 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int tune[5] = {2, 2, 4, 4096, 1};  // GS_TUNE_* launch shapes
+  int tune[6] = {2, 2, 4, 4096, 1, 1};  // GS_TUNE_* launch shapes
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // device error word
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
@@ -139,11 +139,18 @@ inline int bits_for(long long n) {
 }  // namespace gs
 
 namespace gs {
-// Tensor-core level-0 apply (BF16 inverses); see mas_apply_tc.cu.
-bool level0_tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
-int level0_tc_prepare(gs_ctx ctx, gs_mas mas);
-int level0_tc_launch(gs_ctx ctx, gs_mas mas, bool f32_node_major, int nrhs, const void* r, int64_t stride,
-                     const void* zl, int64_t lstride, void* z, const int* skip, int* flags);
+// Level-0 product of the BF16 form (z = W^T (W r) with BF16 inverse Cholesky
+// factors W, FP32 accumulation): tensor cores or FP32 cores; mas_apply_bf16.cu.
+bool level0_bf16_on_tensor_cores(gs_ctx ctx, gs_mas mas, int nrhs);
+int level0_bf16_prepare(gs_ctx ctx, gs_mas mas, const double* fac0);
+int level0_bf16_launch(gs_ctx ctx, gs_mas mas, bool f32_node_major, int nrhs, const void* r, int64_t stride,
+                       const void* zl, int64_t lstride, void* z, const int* skip, int* flags);
+// Level-0 product of the FP64 form on the BF16 tensor cores by exact digit
+// splitting (FP64 accuracy); mas_apply_f64tc.cu.
+bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
+int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas);
+int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
+                        int64_t lstride, double* z);
 }  // namespace gs
 
 struct gs_mat_s {
@@ -176,8 +183,10 @@ struct gs_mas_s {
   int32_t* remap0 = nullptr;       // device int32[n_items[0]], slot -> node or -1
   std::vector<double*> inv64;      // per level: n_domains * (3N)^2
   std::vector<float*> inv32;       // per level (FP32 precision, or made for the mixed solve)
-  std::vector<void*> inv16;        // per level (BF16 precision only; bfloat16 entries)
-  void* inv16_tc = nullptr;        // level 0, BF16, tensor-core operand layout (BF16 precision)
+  std::vector<void*> inv16;        // BF16 precision: level 0 only, inverse Cholesky factor W, row-major
+  void* inv16_tc = nullptr;        // BF16 precision: level-0 W in the tensor-core operand layout
+  void* dig64 = nullptr;           // FP64 precision: level-0 inverses as 7 BF16 digit matrices per domain
+  int32_t* dig64_exp = nullptr;    // FP64 precision: their row exponents
   std::vector<int64_t> vec_off;    // per level l >= 1: offset (in items) into the multilevel vector
   int64_t vec_items = 0;           // total items of levels >= 1
   void** d_inv_tab = nullptr;      // device table: inverse pointer per level (FP64 or FP32)

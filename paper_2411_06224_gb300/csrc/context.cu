@@ -198,6 +198,7 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
     case GS_TUNE_APPLY_RHS: ok = value == 2 || value == 4 || value == 8; break;
     case GS_TUNE_BATCH_CHUNK: ok = value >= 1024 && value <= 16384 && (value & (value - 1)) == 0; break;
     case GS_TUNE_BF16_TC: ok = value == 0 || value == 1; break;
+    case GS_TUNE_F64_TC: ok = value == 0 || value == 1; break;
     default: break;
   }
   GS_CHECK(ok, GS_ERR_INVALID, "gs_tune_set: value %d not allowed for parameter %d", value, param);
@@ -206,7 +207,7 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
 }
 
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value) {
-  GS_CHECK(ctx && value && param >= 0 && param < 5, GS_ERR_INVALID, "gs_tune_get: bad argument");
+  GS_CHECK(ctx && value && param >= 0 && param < 6, GS_ERR_INVALID, "gs_tune_get: bad argument");
   *value = ctx->tune[param];
   return GS_OK;
 }

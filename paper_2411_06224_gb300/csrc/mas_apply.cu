@@ -13,8 +13,6 @@
 // the inverse is symmetric, so row i is read as column i (coalesced).
 #include <cuda_bf16.h>
 
-#include <type_traits>
-
 #include "common.cuh"
 #include "primitives.cuh"
 
@@ -196,9 +194,12 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
                                                                 N, nrhs, rl, zl, lstride, al);
     }
   }
-  if (std::is_same<Ts, __nv_bfloat16>::value && level0_tc_usable(ctx, mas, nrhs)) {
+  if (mas->precision == GS_PREC_BF16) {  // level 0 holds BF16 factors: z = W^T (W r)
     GS_PROF(ctx, GS_K_MAS_APPLY_L0);
-    GS_TRY(level0_tc_launch(ctx, mas, false, nrhs, r, stride, zl, lstride, z, nullptr, ctx->d_flags));
+    GS_TRY(level0_bf16_launch(ctx, mas, false, nrhs, r, stride, zl, lstride, z, nullptr, ctx->d_flags));
+  } else if (level0_f64tc_usable(ctx, mas, nrhs)) {  // FP64 accuracy on the BF16 tensor cores
+    GS_PROF(ctx, GS_K_MAS_APPLY_L0);
+    GS_TRY(level0_f64tc_launch(ctx, mas, nrhs, (const double*)r, stride, (const double*)zl, lstride, (double*)z));
   } else {
     GS_PROF(ctx, GS_K_MAS_APPLY_L0);
 #define GS_L0_ARGS d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al
@@ -215,10 +216,8 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
 }
 
 int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl) {
-  if (mas->precision == GS_PREC_BF16)
-    return launch_apply<__nv_bfloat16, float>(ctx, mas, (const __nv_bfloat16* const*)mas->d_inv_tab,
-                                              mas->d_coarse_jobs, mas->n_coarse_jobs, r, z, nrhs, rl, zl);
-  if (mas->precision == GS_PREC_FP32)
+  // the BF16 form's coarse levels are FP32 inverses
+  if (mas->precision == GS_PREC_FP32 || mas->precision == GS_PREC_BF16)
     return launch_apply<float, float>(ctx, mas, (const float* const*)mas->d_inv_tab, mas->d_coarse_jobs,
                                       mas->n_coarse_jobs, r, z, nrhs, rl, zl);
   return launch_apply<double, double>(ctx, mas, (const double* const*)mas->d_inv_tab, mas->d_coarse_jobs,
@@ -243,7 +242,8 @@ extern "C" int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, 
   double *rl, *zl;
   GS_TRY(gs::mas_level_vectors(ctx, mas, nrhs, &rl, &zl));
   GS_TRY(gs::mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
-  if (gs::level0_tc_usable(ctx, mas, nrhs)) {  // the tensor-core kernel reports bounded-wait timeouts
+  if (gs::level0_bf16_on_tensor_cores(ctx, mas, nrhs) || gs::level0_f64tc_usable(ctx, mas, nrhs)) {
+    // the tensor-core kernels report bounded-wait timeouts
     int flags = 0;
     GS_TRY(ctx->take_flags(&flags));
     if (flags) return gs::status_from_flags(flags);

@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
                                                          const int32_t* __restrict__ remap0, int32_t n_dom0,
                                                          const int32_t* __restrict__ dom_level,
                                                          const int32_t* __restrict__ dom_index,
-                                                         const int32_t* __restrict__ n_items, int N, int* flags) {
+                                                         const int32_t* __restrict__ n_items, int N, int* flags,
+                                                         double* __restrict__ fac0) {
   extern __shared__ double sA[];
   __shared__ int s_lane[32];
   __shared__ int s_k;
@@ -342,6 +343,16 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
     if (tid == 0) sA[j * S + j] = 1.0 / ljj;
     __syncthreads();
   }
+  // level 0, low-precision form: keep the factor W = L^{-1} (M^{-1} = W^T W)
+  if (fac0 && l == 0) {
+    double* F = fac0 + (int64_t)d * ld * ld;
+    for (int e = tid; e < n3 * n3; e += T) {
+      int i = e / n3, j = e % n3;
+      if (j > i) continue;
+      int gi = 3 * s_lane[i / 3] + i % 3, gj = 3 * s_lane[j / 3] + j % 3;
+      F[(int64_t)gi * ld + gj] = sA[i * S + j];
+    }
+  }
   // inverse = W^T W, written over the real part of the global matrix
   for (int e = tid; e < n3 * n3; e += T) {
     int i = e / n3, j = e % n3;
@@ -378,6 +389,8 @@ int gs_mas_destroy(gs_mas mas) {
   for (auto p : mas->inv32) c->release(p);
   for (auto p : mas->inv16) c->release(p);
   c->release(mas->inv16_tc);
+  c->release(mas->dig64);
+  c->release(mas->dig64_exp);
   c->release(mas->remap0);
   c->release(mas->d_inv_tab);
   c->release(mas->d_coarse_jobs);
@@ -526,24 +539,36 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
   const size_t smem = (size_t)(3 * N) * (3 * N + 1) * sizeof(double);
   if (cudaFuncSetAttribute(k_invert_domains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return fail(GS_ERR_CUDA);
-  { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
-                                            ctx->d_flags); }
+  // BF16 form: level 0 keeps its inverse Cholesky factors (rounding W keeps
+  // W^T W positive semi-definite; rounding M^{-1} itself does not once a
+  // domain's condition number passes ~1e3), coarse levels FP32 inverses
+  double* fac0 = nullptr;
+  const int64_t cnt0 = (int64_t)n_dom0 * ld * ld;
   if (opts->precision == GS_PREC_BF16) {
-    for (int l = 0; l < L; ++l) {
-      void* f = nullptr;
-      int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
-      if ((s = ctx->alloc(&f, (size_t)cnt * 2))) return fail(s);
-      mas->inv16.push_back(f);
-      { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_bf16<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], (__nv_bfloat16*)f, cnt); }
-    }
-    if ((s = level0_tc_prepare(ctx, mas))) return fail(s);
+    if ((s = ctx->alloc((void**)&fac0, (size_t)std::max<int64_t>(cnt0, 1) * 8))) return fail(s);
+    if (cudaMemsetAsync(fac0, 0, (size_t)cnt0 * 8, st) != cudaSuccess) return fail(GS_ERR_CUDA);
   }
-  if (opts->precision == GS_PREC_FP32) {
-    for (int l = 0; l < L; ++l) {
+  { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
+                                            ctx->d_flags, fac0); }
+  if (opts->precision == GS_PREC_BF16) {
+    void* f = nullptr;
+    s = ctx->alloc(&f, (size_t)std::max<int64_t>(cnt0, 1) * 2);
+    if (s == GS_OK) {
+      mas->inv16.push_back(f);
+      if (cnt0) { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_bf16<<<ceil_div(cnt0, 256), 256, 0, st>>>(fac0, (__nv_bfloat16*)f, cnt0); }
+      s = level0_bf16_prepare(ctx, mas, fac0);
+    }
+    ctx->release(fac0);
+    if (s) return fail(s);
+  }
+  if (opts->precision == GS_PREC_FP64 && (s = level0_f64tc_prepare(ctx, mas))) return fail(s);
+  if (opts->precision == GS_PREC_FP32 || opts->precision == GS_PREC_BF16) {
+    mas->inv32.assign(L, nullptr);
+    for (int l = opts->precision == GS_PREC_BF16 ? 1 : 0; l < L; ++l) {
       float* f = nullptr;
       int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
       if ((s = ctx->alloc((void**)&f, (size_t)cnt * 4))) return fail(s);
-      mas->inv32.push_back(f);
+      mas->inv32[l] = f;
       { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt); }
     }
   }
@@ -560,7 +585,7 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     std::vector<void*> hp(8, nullptr);
     for (int l = 0; l < L; ++l)
       hp[l] = opts->precision == GS_PREC_FP32   ? (void*)mas->inv32[l]
-              : opts->precision == GS_PREC_BF16 ? mas->inv16[l]
+              : opts->precision == GS_PREC_BF16 ? (l == 0 ? mas->inv16[0] : (void*)mas->inv32[l])
                                                 : (void*)mas->inv64[l];
     std::vector<int32_t> lev, dom;
     for (int l = 1; l < L; ++l)

@@ -485,17 +485,7 @@ static int ensure_f32(gs_ctx ctx, gs_mat m, gs_mas mas, float** au32, std::vecto
     }
   }
   *au32 = m->au32;
-  if (mas->precision == GS_PREC_BF16) {  // the BF16 inverses serve as they are
-    if (!mas->d_inv32_tab) {
-      GS_TRY(ctx->alloc((void**)&mas->d_inv32_tab, 8 * sizeof(void*)));
-      std::vector<void*> hp(8, nullptr);
-      for (int l = 0; l < mas->L; ++l) hp[l] = mas->inv16[l];
-      GS_CUDA(cudaMemcpyAsync(mas->d_inv32_tab, hp.data(), 8 * sizeof(void*), cudaMemcpyHostToDevice, st));
-    }
-    inv.assign(mas->L, nullptr);
-    for (int l = 0; l < mas->L; ++l) inv[l] = (float*)mas->inv16[l];  // opaque pointers, typed at launch
-    return GS_OK;
-  }
+  // BF16 form: inv32 holds the FP32 coarse levels (level 0 is the BF16 factor)
   if (mas->inv32.empty()) {
     const int ld = 3 * mas->N;
     for (int l = 0; l < mas->L; ++l) {
@@ -578,28 +568,19 @@ static int solve_mixed(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int 
       {
         GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
         const int64_t outs = (int64_t)mas->n_coarse_jobs * ld * R;
-        if (bf16)
-          k_coarse32<R, __nv_bfloat16><<<ceil_div(outs, 256), 256, 0, st>>>(
-              (const __nv_bfloat16* const*)mas->d_inv32_tab, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs,
-              mas->n_coarse_jobs, N, al, rl, zl, s);
-        else
-          k_coarse32<R, float><<<ceil_div(outs, 256), 256, 0, st>>>((const float* const*)mas->d_inv32_tab,
-                                                                    mas->d_coarse_jobs,
-                                                                    mas->d_coarse_jobs + mas->n_coarse_jobs,
-                                                                    mas->n_coarse_jobs, N, al, rl, zl, s);
+        k_coarse32<R, float><<<ceil_div(outs, 256), 256, 0, st>>>((const float* const*)mas->d_inv32_tab,
+                                                                  mas->d_coarse_jobs,
+                                                                  mas->d_coarse_jobs + mas->n_coarse_jobs,
+                                                                  mas->n_coarse_jobs, N, al, rl, zl, s);
       }
     }
-    if (bf16 && level0_tc_usable(ctx, mas, R)) {
+    if (bf16) {
       GS_PROF(ctx, GS_K_MAS_APPLY_L0);
-      GS_TRY(level0_tc_launch(ctx, mas, true, R, rr, 0, zl, 0, zz, &s->all_out, &s->flags));
+      GS_TRY(level0_bf16_launch(ctx, mas, true, R, rr, 0, zl, 0, zz, &s->all_out, &s->flags));
     } else {
       GS_PROF(ctx, GS_K_MAS_APPLY_L0);
-      if (bf16)
-        k_level0_32<R, __nv_bfloat16><<<mas->n_domains[0], lv0_threads, lv0_smem, st>>>(
-            (const __nv_bfloat16*)inv[0], mas->remap0, N, al, rr, zl, zz, s);
-      else
-        k_level0_32<R, float><<<mas->n_domains[0], lv0_threads, lv0_smem, st>>>(inv[0], mas->remap0, N, al, rr, zl,
-                                                                                zz, s);
+      k_level0_32<R, float><<<mas->n_domains[0], lv0_threads, lv0_smem, st>>>(inv[0], mas->remap0, N, al, rr, zl,
+                                                                              zz, s);
     }
     return GS_OK;
   };

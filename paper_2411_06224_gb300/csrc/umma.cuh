@@ -89,7 +89,7 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp gets lane
 // (lane field of taddr) + t, columns col .. col + 15.
-__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float (&v)[16]) {
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -103,10 +103,11 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float (&v)[16
 }
 
 // ------------------------------------------------------------------ MMA
-// Shared-memory matrix descriptor, no swizzle.  Canonical K-major layout:
-// core matrices of 8 rows x 16 bytes (128 contiguous bytes, rows 16 bytes
-// apart); `lbo` = byte distance between core matrices adjacent along K,
-// `sbo` = along M (or N).
+// Shared-memory matrix descriptor, no swizzle.  Core matrices are 8 rows x
+// 16 bytes (128 contiguous bytes, rows 16 bytes apart): for a K-major operand
+// a row runs along K, for an MN-major one along M (or N).  Either way `lbo`
+// is the byte distance between core matrices adjacent along K and `sbo` the
+// distance between core matrices adjacent along M (or N).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;

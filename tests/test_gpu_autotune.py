@@ -52,13 +52,13 @@ def build(B, ctx, s, N=16, L=3, node_off=None):
 def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
-                       (7, 2)):
+                       (B.GS_TUNE_F64_TC, 3), (7, 2)):
         with pytest.raises(B.GsError):
             B.gs_tune_set(ctx, param, bad)
     from paper_2411_06224_gb300 import autotune
 
     assert autotune.current(ctx) == {"spmv_lanes": 2, "apply_rhs_per_thread": 4, "spmv32_lanes": 2,
-                                     "batch_chunk": 4096, "bf16_tensor_cores": 1}
+                                     "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1}
 
 
 def test_every_shape_gives_the_oracle_result(B, ctx):
@@ -80,10 +80,14 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
         B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs)
         assert np.all(np.abs(y.cpu().numpy() - Ax) <= bound), lanes
     zs = {}
+    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 0)  # the RHS-per-thread shape belongs to the FP64-core kernel
     for rpt in autotune.CANDIDATES[B.GS_TUNE_APPLY_RHS]:
         B.gs_tune_set(ctx, B.GS_TUNE_APPLY_RHS, rpt)
         B.gs_mas_apply(ctx, M, xd, y, nrhs=nrhs)
         zs[rpt] = y.cpu().numpy()
+    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 1)
+    B.gs_mas_apply(ctx, M, xd, y, nrhs=nrhs)
+    zs["tensor_cores"] = y.cpu().numpy()
     z0 = np.stack([Mo(v) for v in x])
     for rpt, z in zs.items():
         np.testing.assert_allclose(z, zs[4], rtol=1e-10, atol=1e-12 * np.abs(zs[4]).max())
@@ -95,8 +99,8 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
         B.gs_pcg_solve_mixed(ctx, mat, M, dev(b, torch.float64), xm, nrhs=4, tol=1e-6)
         for k, xk in enumerate(xm.cpu().numpy()):
             assert np.linalg.norm(b[k] - A(xk)) <= 1.05e-6 * np.linalg.norm(b[k]), lanes
-    best = autotune.tune(ctx, mat, M, nrhs=nrhs, reps=3, mixed=True)
-    assert set(best) == {"spmv_lanes", "apply_rhs_per_thread", "spmv32_lanes"}
+    best = autotune.tune(ctx, mat, M, nrhs=nrhs, reps=3, mixed=True, fp64=True)
+    assert {"spmv_lanes", "fp64_on_tensor_cores", "spmv32_lanes"} <= set(best)
     cur = autotune.current(ctx)
     for name, (v, times) in best.items():
         assert cur[name] == v and v in times and times[v] == min(times.values()) and times[v] > 0

@@ -1,5 +1,6 @@
-"""Low-precision MAS inverses (FP32, BF16 storage; FP32 accumulation) against the
-FP64 oracle with its inverses rounded the same way, and the precision forms
+"""Low-precision MAS forms (FP32 inverses; BF16 inverse Cholesky factors at
+level 0; FP32 accumulation) against the FP64 oracle's levels with the same
+roundings applied, and the precision forms
 on a stiff cloth sheet (cubic strain limiting, E = 1e8): every solve must
 reach the 1e-6 true residual and agree with the oracle's FP64 solution."""
 
@@ -7,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import lowprec
 from oracle import assembly, mas, partition, pcg
 from synth.cloth import make_cloth_system
 from synth.workloads import make_tet_system, rhs
@@ -35,17 +37,6 @@ def dev(a, dt):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
 
 
-def round_f32(a):
-    return np.asarray(a).astype(np.float32).astype(np.float64)
-
-
-def round_bf16(a):
-    """double -> float -> bfloat16 with round-to-nearest-even, back to double."""
-    f = np.asarray(a).astype(np.float32).view(np.uint32)
-    f = (f + (((f >> 16) & 1) + 0x7FFF)) & 0xFFFF0000
-    return f.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
 @pytest.fixture(scope="module")
 def cloth():
     return make_cloth_system(48, seed=5)
@@ -62,13 +53,12 @@ def test_low_precision_apply_matches_rounded_oracle(B, ctx, cloth, prec, name):
                        dev(s.contacts, torch.int32), domain_size=N, max_levels=L, precision=prec)
     rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
     om = mas.build_mas(mp, N, L, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
-    rnd = round_f32 if prec == 1 else round_bf16
-    inv_r = [rnd(v) for v in om.invs]
+    ops, ops_abs = lowprec.effective_inverses(om, prec)
     r = np.random.default_rng(prec).normal(size=(nrhs, 3 * V))
     z = torch.empty((nrhs, 3 * V), dtype=torch.float64, device="cuda")
     B.gs_mas_apply(ctx, M, dev(r, torch.float64), z, nrhs=nrhs)
-    z0 = mas.apply(om.levels, inv_r, r, om.C)
-    bound = 1e-5 * mas.apply(om.levels, [np.abs(v) for v in inv_r], np.abs(r), om.C)
+    z0 = mas.apply(om.levels, ops, r, om.C)
+    bound = lowprec.BOUND * mas.apply(om.levels, ops_abs, np.abs(r), om.C)
     assert np.all(np.abs(z.cpu().numpy() - z0) <= bound + 1e-300)
     B.gs_mas_destroy(M)
     B.gs_mat_destroy(mat)

@@ -512,3 +512,25 @@ def test_strain_limit_is_c2_at_the_limit():
         assert np.abs(sl.gradient(Fe, sl.N_U)).max() < 4 * eps ** 2
         assert np.abs(sl.hessian(Fe, sl.N_U)).max() < 20 * eps
     assert sl.energy(F * 0.9, sl.N_U) == 0.0 and not sl.hessian(F * 0.9, sl.N_U).any()
+
+
+def test_inverse_factors_reproduce_the_inverses():
+    # M_d^{-1} = W^T W with W = L^{-1} lower triangular (the BF16 storage form)
+    s = _tiny_system(n=5, E=1e6, contacts=6, seed=21)
+    rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
+    part = partition.recursive_bisection(s.X, 8)
+    mp, _ = partition.map_remap(part, 8)
+    lv = mas.build_levels(mp, 8, 3, s.adj_ptr, s.adj, s.contacts)
+    mats = mas.level_matrices(lv, rid, cid, au)
+    invs = mas.invert_domains(lv, mats)
+    facs = mas.inverse_factors(lv, mats)
+    for l, (inv, fac) in enumerate(zip(invs, facs)):
+        for d in range(inv.shape[0]):
+            assert np.allclose(np.triu(fac[d], 1), 0.0)
+            np.testing.assert_allclose(fac[d].T @ fac[d], inv[d], rtol=1e-10, atol=1e-12 * np.abs(inv[d]).max())
+            # W M_d W^T = I on the real part (and 0 on the padding)
+            real = np.any(fac[d] != 0, axis=1)
+            if not real.any():
+                continue
+            WMW = fac[d] @ mats[l][d] @ fac[d].T
+            np.testing.assert_allclose(WMW[np.ix_(real, real)], np.eye(real.sum()), atol=1e-9)
