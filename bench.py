@@ -19,6 +19,7 @@ host memory every step and the solutions copied back.
 """
 
 import argparse
+from concurrent.futures import ThreadPoolExecutor
 import json
 import os
 import statistics
@@ -55,6 +56,8 @@ def parse():
     p.add_argument("--spmv", default="row", choices=["row", "srbk"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
+    p.add_argument("--no-lanes", dest="lanes", action="store_false",
+                   help="solve the systems of a step one after another on one stream")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default launch shapes instead of tuning them first")
     p.add_argument("--batch-steps", type=int, default=2, help="timed steps of the batched form (64 uneven systems)")
@@ -217,21 +220,66 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = B.gs_create(local, stream)
 
-    def solve_one(rows, cols, blocks, bb, xx):
-        mat = B.gs_assemble(ctx, V, rows, cols, blocks)
-        mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
+    def solve_one(rows, cols, blocks, bb, xx, c=None):
+        c = c or ctx
+        mat = B.gs_assemble(c, V, rows, cols, blocks)
+        mas = B.gs_build_mas(c, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
                              domain_size=N, max_levels=L, precision=prec)
-        it, rel, _ = B.gs_pcg_solve(ctx, mat, mas, bb, xx, nrhs=args.nrhs, tol=TOL, max_iter=20000, variant=variant)
+        it, rel, _ = B.gs_pcg_solve(c, mat, mas, bb, xx, nrhs=args.nrhs, tol=TOL, max_iter=20000, variant=variant)
         info = (B.gs_mat_info(mat)[1], B.gs_mas_info(mas))
         B.gs_mas_destroy(mas)
         B.gs_mat_destroy(mat)
         return it, rel, info
 
+    # The systems of a step are independent Newton solves.  With --lanes (the
+    # default) each runs on its own library context and CUDA stream, driven by
+    # its own host thread, so the FP64-pipe-bound SpMV of one system overlaps
+    # the HBM- and tensor-bound MAS apply of another.
+    n_lanes = len(dsys) if args.lanes else 1
+    lane_streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)] if args.lanes else [stream]
+    lane_ctx = [B.gs_create(local, s_) for s_ in lane_streams] if args.lanes else [ctx]
+    lane_x = [torch.zeros_like(b) for _ in range(n_lanes)] if args.lanes else [x]
+    pool = ThreadPoolExecutor(max_workers=n_lanes)
+
+    def fork():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for s_ in lane_streams:
+            s_.wait_event(ev)
+
+    def join():
+        for s_ in lane_streams:
+            ev = torch.cuda.Event()
+            ev.record(s_)
+            stream.wait_event(ev)
+
+    def lane_run(i, fn):
+        torch.cuda.set_device(local)
+        with torch.cuda.stream(lane_streams[i]):
+            return fn(i)
+
     def step():
-        out = []
-        for s in dsys:
-            out.append(solve_one(s["rows"], s["cols"], s["blocks"], b, x))
+        if n_lanes == 1:
+            return [solve_one(s["rows"], s["cols"], s["blocks"], b, x) for s in dsys]
+        fork()
+        futs = [pool.submit(lane_run, i, lambda i, s=s: solve_one(s["rows"], s["cols"], s["blocks"], b, lane_x[i],
+                                                                   lane_ctx[i]))
+                for i, s in enumerate(dsys)]
+        out = [f.result() for f in futs]
+        join()
         return out
+
+    def profile_begin(classes):
+        for c in lane_ctx:
+            B.gs_profile_begin(c, classes)
+
+    def profile_end():
+        tot_l, tot_ms = None, None
+        for c in lane_ctx:
+            l_, m_ = B.gs_profile_end(c)
+            tot_l = l_ if tot_l is None else tot_l + l_
+            tot_ms = m_ if tot_ms is None else tot_ms + m_
+        return tot_l, tot_ms
 
     def barrier():
         if world > 1:
@@ -262,6 +310,9 @@ def main():
         tuned = {k: {"best": v[0], "ms_per_launch": {str(c): round(m, 4) for c, m in v[1].items()}}
                  for k, v in res.items()}
         B.gs_mat_destroy(mat)
+        for c in lane_ctx:  # every lane uses the tuned shapes
+            for prm in autotune.CANDIDATES:
+                B.gs_tune_set(c, prm, B.gs_tune_get(ctx, prm))
 
     # warm-up
     for _ in range(args.warmup):
@@ -270,9 +321,9 @@ def main():
     nnzb = warm[0][2][0]
     mas_levels = warm[0][2][1]
     # per-class breakdown of one step (all classes timed with events; outside the timed region)
-    B.gs_profile_begin(ctx, range(B.GS_K_COUNT))
+    profile_begin(range(B.GS_K_COUNT))
     step()
-    launches_1, ms_1 = B.gs_profile_end(ctx)
+    launches_1, ms_1 = profile_end()
 
     # timed region: the dominant kernels are bracketed by CUDA events on the library's stream
     timed_classes = [B.GS_K_MAS_APPLY_L0, B.GS_K_SPMV]
@@ -280,7 +331,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    B.gs_profile_begin(ctx, timed_classes)
+    profile_begin(timed_classes)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     w0 = time.perf_counter()
@@ -290,7 +341,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
-    launches, kms = B.gs_profile_end(ctx)
+    launches, kms = profile_end()
     barrier()
     clk = clocks.stop()
     from paper_2411_06224_gb300 import replicas
@@ -300,6 +351,8 @@ def main():
 
     # true residuals of the last step (checked on the device through the library's SpMV)
     true_rel = []
+    if n_lanes > 1:
+        x.copy_(lane_x[-1])
     Ax = torch.empty_like(x)
     for s in dsys[-1:]:
         mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
@@ -321,16 +374,28 @@ def main():
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        hxs = [torch.empty_like(hb).pin_memory() for _ in hsys]
+
+        def e2e_one(i, h, c):
+            rows = h["rows"].to(dev, non_blocking=True)
+            cols = h["cols"].to(dev, non_blocking=True)
+            blocks = h["blocks"].to(dev, non_blocking=True)
+            bb = hb.to(dev, non_blocking=True)
+            xx = torch.empty_like(bb)
+            solve_one(rows, cols, blocks, bb, xx, c)
+            hxs[i].copy_(xx, non_blocking=True)
+            torch.cuda.current_stream().synchronize()  # the host holds the answer
+
         f0.record(stream)
         for _ in range(args.e2e_steps):
-            for h in hsys:
-                rows = h["rows"].to(dev, non_blocking=True)
-                cols = h["cols"].to(dev, non_blocking=True)
-                blocks = h["blocks"].to(dev, non_blocking=True)
-                bb = hb.to(dev, non_blocking=True)
-                xx = torch.empty_like(bb)
-                solve_one(rows, cols, blocks, bb, xx)
-                hx.copy_(xx, non_blocking=True)
+            if n_lanes == 1:
+                for i, h in enumerate(hsys):
+                    e2e_one(i, h, ctx)
+            else:
+                fork()
+                futs = [pool.submit(lane_run, i, lambda i, h=h: e2e_one(i, h, lane_ctx[i])) for i, h in enumerate(hsys)]
+                [f.result() for f in futs]
+                join()
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_rate, el = replicas.throughput(len(hsys) * args.e2e_steps, f0.elapsed_time(f1) / 1e3, dev)
