@@ -286,9 +286,10 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 #define GS_TUNE_BATCH_CHUNK 3     /* vector entries per work item of the batched reductions: 1024..16384 (4096) */
 #define GS_TUNE_BF16_TC 4         /* BF16 level-0 apply on the tensor cores (1, default) or on FP32 cores (0);
                                      the tensor-core form needs 3N a multiple of 16 (N = 16, 32) and nrhs <= 8 */
-#define GS_TUNE_F64_TC 5          /* FP64 level-0 apply on the BF16 tensor cores by exact digit splitting (1,
-                                     default; FP64 accuracy) or on the FP64 cores (0); needs 3N a multiple
-                                     of 16 and nrhs <= 8 */
+#define GS_TUNE_F64_TC 5          /* FP64 MAS apply on the BF16 tensor cores by exact digit splitting (FP64
+                                     accuracy): 1 (default) one CTA per domain, 2 one persistent warp-
+                                     specialised CTA per SM for level 0; 0 on the FP64 cores.  Needs 3N a
+                                     multiple of 16 and nrhs <= 8 */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
 

@@ -15,8 +15,9 @@ The shapes and the kernels they steer:
   * GS_TUNE_SPMV32_LANES lanes per block row of the FP32 SpMV inside the mixed solve;
   * GS_TUNE_BATCH_CHUNK  vector entries per work item of the batched PCG reductions;
   * GS_TUNE_BF16_TC      BF16 level-0 apply on the tensor cores or on the FP32 cores;
-  * GS_TUNE_F64_TC       FP64 level-0 apply on the BF16 tensor cores (exact digit
-                         splitting) or on the FP64 cores.
+  * GS_TUNE_F64_TC       FP64 apply on the BF16 tensor cores (exact digit
+                         splitting; one CTA per domain or one persistent CTA
+                         per SM) or on the FP64 cores.
 """
 
 import torch
@@ -29,7 +30,7 @@ CANDIDATES = {
     B.GS_TUNE_SPMV32_LANES: (2, 4),
     B.GS_TUNE_BATCH_CHUNK: (1024, 2048, 4096, 8192, 16384),
     B.GS_TUNE_BF16_TC: (1, 0),
-    B.GS_TUNE_F64_TC: (1, 0),
+    B.GS_TUNE_F64_TC: (1, 2, 0),
 }
 
 NAMES = {

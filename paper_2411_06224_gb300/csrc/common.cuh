@@ -151,6 +151,7 @@ bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas);
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
                         int64_t lstride, double* z);
+int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride);
 }  // namespace gs
 
 struct gs_mat_s {
@@ -185,8 +186,9 @@ struct gs_mas_s {
   std::vector<float*> inv32;       // per level (FP32 precision, or made for the mixed solve)
   std::vector<void*> inv16;        // BF16 precision: level 0 only, inverse Cholesky factor W, row-major
   void* inv16_tc = nullptr;        // BF16 precision: level-0 W in the tensor-core operand layout
-  void* dig64 = nullptr;           // FP64 precision: level-0 inverses as 7 BF16 digit matrices per domain
-  int32_t* dig64_exp = nullptr;    // FP64 precision: their row exponents
+  std::vector<void*> dig64;        // FP64 precision: per level, the inverses as 7 BF16 digit matrices per domain
+  std::vector<int32_t*> dig64_exp; // FP64 precision: per level, their row exponents
+  void** d_dig_tab = nullptr;      // device table: digit pointers [0..7], exponent pointers [8..15]
   std::vector<int64_t> vec_off;    // per level l >= 1: offset (in items) into the multilevel vector
   int64_t vec_items = 0;           // total items of levels >= 1
   void** d_inv_tab = nullptr;      // device table: inverse pointer per level (FP64 or FP32)

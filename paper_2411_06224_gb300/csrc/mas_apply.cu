@@ -187,7 +187,10 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
     { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div(mas->n_domains[0], kRestrictWarps), 32 * kRestrictWarps, 0, st>>>(r, stride, nrhs, mas->remap0,
                                                                               mas->n_domains[0], al, rl, lstride); }
-    {
+    if (level0_f64tc_usable(ctx, mas, nrhs)) {  // FP64 accuracy on the BF16 tensor cores
+      GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
+      GS_TRY(coarse_f64tc_launch(ctx, mas, nrhs, rl, zl, lstride));
+    } else {
       GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
       const int64_t outs = (int64_t)n_coarse_jobs * ld * nrhs;
       k_coarse_product<Ts, Tm><<<ceil_div(outs, 256), 256, 0, st>>>(d_inv, d_jobs, d_jobs + n_coarse_jobs, n_coarse_jobs,

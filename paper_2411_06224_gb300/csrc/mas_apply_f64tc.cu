@@ -17,15 +17,18 @@
 //     accumulates each G_s in its own 8 TMEM columns, one MMA per (digit p,
 //     pair of digits q, q+1) with N = 16;
 //   * z_ik = 2^(a_i + b_k - 72) sum_{s=2..9} G_s 256^(9-s), combined in
-//     64-bit integers (two halves) and converted once.
+//     64-bit integers (two halves) and rounded once to a double in integer
+//     arithmetic, so the epilogue spends one FP64 add (the coarse levels).
 // Dropped terms (p + q > 9) and the roundings of X, Y are below 2^-55 of the
 // row and column maxima, the level of FP64's own rounding.
 //
 // One CTA per domain, 128 threads; the 7 digit matrices (18 KB each) stream
-// through a 4-slot shared-memory ring filled by bulk asynchronous copies, so
-// two CTAs fit on an SM and one's epilogue overlaps the other's copies.  All
+// through a 2-slot shared-memory ring filled by bulk asynchronous copies
+// (50 KB per CTA), so four CTAs share an SM and hide each other's latency.  All
 // waits are bounded (kErrTimeout); TMEM is always freed.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -34,7 +37,7 @@ namespace gs {
 namespace f64tc {
 
 constexpr int kDigits = 7;
-constexpr int kSlots = 4;
+constexpr int kSlots = 2;
 constexpr int kThreads = 128;
 constexpr int kM = 128;
 constexpr int kTmemCols = 128;  // groups s = 2..10, 8 columns each (72 used)
@@ -50,12 +53,33 @@ __host__ __device__ inline uint32_t slot_bytes(int ld) {  // K-major M = 128 spa
 }
 __host__ __device__ inline uint32_t b_bytes(int ld) { return (uint32_t)(ld / 8) * 256; }
 __host__ inline size_t smem_bytes(int ld) {
-  return 128 + (size_t)kSlots * slot_bytes(ld) + 4 * (size_t)b_bytes(ld) + (2 * kSlots + 1) * 8 + 8 + 8 * 4;
+  return 128 + (size_t)kSlots * slot_bytes(ld) + 4 * (size_t)b_bytes(ld) + (2 * kSlots + 1) * 8 + 8 + 8 * 4 + 32 * 4;
 }
 
-// 2^e as a double for e in the normal range (bit construction).
-__device__ __forceinline__ double pow2(int e) {
-  return __longlong_as_double((long long)(e + 1023) << 52);
+// T 2^e as the nearest double (ties to even), T = hi 2^32 + lo with
+// |hi|, |lo| < 2^49, in integer arithmetic only: the 128-bit magnitude is
+// normalised, rounded to 53 bits and packed with its exponent.  Results
+// below the normal range flush to zero.
+__device__ __forceinline__ double scaled_to_double(long long hi, long long lo, int e) {
+  __int128 T = ((__int128)hi << 32) + (__int128)lo;
+  if (T == 0) return 0.0;
+  const unsigned long long sign = T < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned __int128 M = (unsigned __int128)(T < 0 ? -T : T);
+  const unsigned long long top = (unsigned long long)(M >> 64);
+  const int lz = top ? __clzll(top) : 64 + __clzll((unsigned long long)M);
+  M <<= lz;  // leading one at bit 127
+  unsigned long long mant = (unsigned long long)(M >> 75);  // 53 bits
+  const unsigned __int128 rest = M & ((((unsigned __int128)1) << 75) - 1);
+  const unsigned __int128 half = ((unsigned __int128)1) << 74;
+  int E = 127 - lz + e;  // value = 1.f 2^E
+  if (rest > half || (rest == half && (mant & 1))) {
+    if (++mant == (1ULL << 53)) {
+      mant >>= 1;
+      ++E;
+    }
+  }
+  if (E < -1022) return 0.0;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
 }
 
 // Biased exponent field of a double (0 for zero / subnormal).
@@ -124,8 +148,15 @@ __global__ void k_split_inverse(const double* __restrict__ inv, int ld, __nv_bfl
 // groups s = p + 2j + 2 and s + 1 (1-based digits p+1 and 2j+1, 2j+2)
 __device__ __forceinline__ int pairs_for(int p) { return (8 - (p + 1)) / 2 + 1; }
 
-__global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* __restrict__ dig,
-                                                           const int32_t* __restrict__ row_exp,
+// kCoarse = false: level 0, CTA = level-0 domain, r gathered through remap0,
+//   z = level-0 product + prolongated coarse results, written per node;
+// kCoarse = true: one coarse-level domain per CTA (job tables), r and z are the
+//   level's contiguous multilevel vectors rl, zl.
+template <bool kCoarse>
+__global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* const* __restrict__ dig_tab,
+                                                           const int32_t* const* __restrict__ exp_tab,
+                                                           const int32_t* __restrict__ job_level,
+                                                           const int32_t* __restrict__ job_dom,
                                                            const int32_t* __restrict__ remap0, int N, int nrhs,
                                                            Levels al, const double* __restrict__ r, int64_t stride,
                                                            const double* __restrict__ zl, int64_t lstride,
@@ -142,10 +173,14 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   uint64_t* done = empty + kSlots;
   uint32_t* tslot = (uint32_t*)(done + 1);
   int* sfail = (int*)(tslot + 1);
-  int* sexp = sfail + 1;  // [8] biased exponent maxima of the RHS columns
+  int* sexp = sfail + 1;   // [8] biased exponent maxima of the RHS columns
+  int* snode = sexp + 8;   // [32] node of every slot of the domain (-1: padding)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int32_t d = blockIdx.x;
-  const __nv_bfloat16* dd = dig + (int64_t)d * kDigits * ld * ld;
+  const int lvl = kCoarse ? job_level[blockIdx.x] : 0;
+  const int32_t d = kCoarse ? job_dom[blockIdx.x] : (int32_t)blockIdx.x;
+  const __nv_bfloat16* dd = dig_tab[lvl] + (int64_t)d * kDigits * ld * ld;
+  const int32_t* row_exp = exp_tab[lvl];
+  const int64_t cbase = kCoarse ? 3 * (al.vec_off[lvl] + (int64_t)d * N) : 0;  // coarse: first entry of the domain
 
   if (tid == 0) {
     for (int s = 0; s < kSlots; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], 1);
@@ -154,6 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     fence_mbar_init();
   }
   if (tid < 8) sexp[tid] = 0;
+  if (tid < 32) snode[tid] = tid < N ? (kCoarse ? 0 : remap0[(int64_t)d * N + tid]) : -1;
   if (warp == 0) {
     tmem_alloc(tslot, kTmemCols);
     tmem_relinquish();
@@ -162,29 +198,38 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  if (tid == 0)
+  if (tid == 0) {
     for (int p = 0; p < kSlots; ++p) {
       mbar_arrive_expect_tx(&full[p], dig_bytes);
       bulk_g2s(ring + p * sbytes, dd + (int64_t)p * ld * ld, dig_bytes, &full[p]);
     }
-  // column exponents of r_d (RHS k < 8; columns >= nrhs stay 0)
-  const int nv = ld * 8;
-  for (int e = tid; e < nv; e += kThreads) {
+  }
+  // r_d once into registers (entry e = k * ld + j), column exponents by
+  // shared-memory atomics, then the digits into the four pair operands
+  constexpr int kPer = 8 * 128 / kThreads;  // entries per thread for ld <= 128
+  double rv[kPer];
+#pragma unroll
+  for (int m = 0; m < kPer; ++m) {
+    const int e = tid + m * kThreads;
     const int k = e / ld, j = e - k * ld;
-    if (k >= nrhs) continue;
-    const int32_t node = remap0[(int64_t)d * N + j / 3];
-    if (node >= 0) atomicMax(&sexp[k], biased_exp(r[k * stride + 3 * (int64_t)node + j % 3]));
+    rv[m] = 0.0;
+    if (k < nrhs && k < 8) {
+      const int32_t node = snode[j / 3];
+      if (kCoarse)
+        rv[m] = r[k * lstride + cbase + j];
+      else if (node >= 0)
+        rv[m] = r[k * stride + 3 * (int64_t)node + j % 3];
+      if (rv[m] != 0.0) atomicMax(&sexp[k], biased_exp(rv[m]));
+    }
   }
   __syncthreads();
-  // digits of r_d into the four pair operands; element (n, kk) of a pair
-  // operand at (kk/8)*256 + (n/8)*128 + (n%8)*16 + (kk%8)*2
-  for (int e = tid; e < nv; e += kThreads) {
+  // element (n, kk) of a pair operand at (kk/8)*256 + (n/8)*128 + (n%8)*16 + (kk%8)*2
+#pragma unroll
+  for (int m = 0; m < kPer; ++m) {
+    const int e = tid + m * kThreads;
+    if (e >= 8 * ld) break;
     const int k = e / ld, j = e - k * ld;
-    long long y = 0;
-    if (k < nrhs && sexp[k]) {
-      const int32_t node = remap0[(int64_t)d * N + j / 3];
-      if (node >= 0) y = scaled_rint(r[k * stride + 3 * (int64_t)node + j % 3], sexp[k] - 1021);
-    }
+    const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], sexp[k] - 1021) : 0;
     int dg[kDigits];
     digits(y, dg);
     unsigned char* col = sB + (j >> 3) * 256 + (j & 7) * 2 + k * 16;
@@ -194,14 +239,42 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   }
   fence_proxy_async();
   __syncthreads();
+  // Epilogue operands that do not depend on the MMAs, loaded now so that their
+  // latency overlaps the tensor-core work: row exponent and the prolongated
+  // coarse-level sum per RHS.
+  const int i_row = warp * 32 + lane;
+  const int32_t node_row = (warp * 32 < ld && i_row < ld) ? snode[i_row / 3] : -1;
+  int a_row = -100000;
+  double coarse_sum[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) coarse_sum[k] = 0.0;
+  if (node_row >= 0) {
+    a_row = row_exp[(int64_t)d * ld + i_row];
+  }
+  if (!kCoarse && node_row >= 0) {
+    const int c = i_row % 3;
+#pragma unroll
+    for (int l = 1; l < 8; ++l) {
+      if (l >= al.L) break;
+      const int64_t item = al.vec_off[l] + al.coarse[l][node_row];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < nrhs) coarse_sum[k] += zl[k * lstride + 3 * item + c];
+    }
+  }
   // MMA issue and ring refills (one thread).  A slot is refilled one digit
   // later than its MMAs were issued, so the tensor core is not waited on.
+  // Descriptors are built once; their 14-bit address fields are advanced by
+  // adding byte offsets / 16 (all addresses stay below 256 KB).
   if (tid == 0) {
     bool ok = true;
-    int refilled = 0;  // bit s: slot s holds a second digit matrix
+    int loads[kSlots];  // copies issued into each slot
+    for (int s = 0; s < kSlots; ++s) loads[s] = 1;
     const uint32_t lbo = (uint32_t)ld * 16;
     const uint32_t idesc = idesc_bf16_f32(kM, 16);
-    const uint32_t b0 = smem_u32(sB);
+    const uint64_t da0 = smem_desc(smem_u32(ring), lbo, 128);
+    const uint64_t db0 = smem_desc(smem_u32(sB), 256, 128);
+    const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 512u >> 4, db_j = bb >> 4;
     for (int p = 0; p < kDigits && ok; ++p) {
       const int slot = p % kSlots;
       if (!mbar_wait(&full[slot], (uint32_t)(p / kSlots) & 1u)) {
@@ -209,22 +282,25 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
         break;
       }
       fence_after_sync();
-      const uint32_t a0 = smem_u32(ring + slot * sbytes);
-      for (int j = 0; j < pairs_for(p); ++j)
+      const uint64_t da = da0 + ((uint64_t)slot * sbytes >> 4);
+      for (int j = 0; j < pairs_for(p); ++j) {
+        const uint32_t dcol = tmem + 8u * (p + 2 * j);
+        const uint64_t db = db0 + j * db_j;
+#pragma unroll 6
         for (int ks = 0; ks < ld / 16; ++ks)
-          mma_bf16(tmem + 8u * (p + 2 * j), smem_desc(a0 + 2u * ks * lbo, lbo, 128),
-                   smem_desc(b0 + j * bb + 512u * ks, 256, 128), idesc, (p > 0 || ks > 0) ? 1u : 0u);
+          mma_bf16(dcol, da + ks * da_ks, db + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
+      }
       mma_commit(&empty[slot]);
       const int q = p - 1;  // the previous digit's slot takes digit q + kSlots
       if (q >= 0 && q + kSlots < kDigits) {
         const int qs = q % kSlots;
-        if (!mbar_wait(&empty[qs], 0)) {
+        if (!mbar_wait(&empty[qs], (uint32_t)(q / kSlots) & 1u)) {
           ok = false;
           break;
         }
         mbar_arrive_expect_tx(&full[qs], dig_bytes);
         bulk_g2s(ring + qs * sbytes, dd + (int64_t)(q + kSlots) * ld * ld, dig_bytes, &full[qs]);
-        refilled |= 1 << qs;
+        ++loads[qs];
       }
     }
     if (ok) {
@@ -232,10 +308,8 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     } else {
       *sfail = 1;
       atomicOr(flags, kErrTimeout);
-      for (int s = 0; s < kSlots; ++s) {  // let copies in flight land before the CTA leaves
-        mbar_wait(&full[s], 0);
-        if (refilled & (1 << s)) mbar_wait(&full[s], 1);
-      }
+      for (int s = 0; s < kSlots; ++s)  // let the last copy into each slot land before the CTA leaves
+        mbar_wait(&full[s], (uint32_t)(loads[s] - 1) & 1u);
       mbar_arrive(done);
     }
   }
@@ -251,14 +325,10 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     tmem_ld_32x32b_x16(ta + 16, g + 16);
     tmem_ld_32x32b_x16(ta + 32, g + 32);
     tmem_ld_32x32b_x16(ta + 48, g + 48);
-    const int i = warp * 32 + lane;
-    const int32_t node = i < ld ? remap0[(int64_t)d * N + i / 3] : -1;
+    const int32_t node = node_row;
     if (node >= 0) {
-      const int a = row_exp[(int64_t)d * ld + i];
-      const int c = i % 3;
-      int64_t citem[8];
-#pragma unroll
-      for (int l = 1; l < 8; ++l) citem[l] = l < al.L ? al.vec_off[l] + al.coarse[l][node] : 0;
+      const int a = a_row;
+      const int c = i_row % 3;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (k >= nrhs) break;
@@ -270,14 +340,13 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
           for (int s = 0; s < 4; ++s) hi = (hi << 8) + (long long)__float2int_rn(g[8 * s + k]);
 #pragma unroll
           for (int s = 4; s < 8; ++s) lo = (lo << 8) + (long long)__float2int_rn(g[8 * s + k]);
-          const int e = a + (sexp[k] - 1021) - 72;  // z = T 2^e
-          if (e > -1000 && e < 900)                    // outside: |z| underflows (or overflows) FP64
-            v = fma((double)hi, pow2(e + 32), (double)lo * pow2(e));
+          const int e = a + (sexp[k] - 1021) - 72;  // z = T 2^e, T = hi 2^32 + lo
+          if (e < 900) v = scaled_to_double(hi, lo, e);
         }
-#pragma unroll
-        for (int l = 1; l < 8; ++l)
-          if (l < al.L) v += zl[k * lstride + 3 * citem[l] + c];
-        z[k * stride + 3 * (int64_t)node + c] = v;
+        if (kCoarse)
+          z[k * lstride + cbase + i_row] = v;
+        else
+          z[k * stride + 3 * (int64_t)node + c] = v + coarse_sum[k];
       }
     }
   }
@@ -289,41 +358,372 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   }
 }
 
+
+// ---------------------------------------------------------------- persistent form
+// One CTA per SM walks domains d = blockIdx.x, + gridDim.x, ...  Warp roles:
+//   warp 0 (one lane)  producer: streams the 7 digit matrices of domain after
+//                      domain through a kRing-slot shared-memory ring;
+//   warp 1 (one lane)  MMA issuer: group sums of domain n into TMEM buffer n%2;
+//   warps 2-3          stagers: r of domain n -> column exponents and digits
+//                      into B-operand buffer n%2;
+//   warps 4-7          epilogue: TMEM lane quarter (warp % 4), rounding to
+//                      FP64, prolongated coarse sums, z.
+// Barriers (phase parity = use count & 1): ring full/empty per slot, B-buffer
+// full/empty (empty needs the MMAs and the epilogue), TMEM full/empty.  Copies,
+// MMAs, staging and epilogue of consecutive domains overlap.  Every wait is
+// bounded; a timeout sets an abort word that every role checks, so all roles
+// leave their loops, wait (bounded) for their asynchronous work and meet at
+// the final barrier that precedes the TMEM release.
+constexpr int kRing = 10;
+constexpr int kPThreads = 256;
+
+// Layout after the 128-byte alignment slack: ring, B buffers [2][4], barriers
+// (full, empty [kRing]; bfull, bempty, tfull, tempty [2]; drain), a 64-byte
+// word area (TMEM address, abort word), exponents [2][8], node map [2][32].
+__host__ inline size_t psmem_bytes(int ld) {
+  return 128 + (size_t)kRing * slot_bytes(ld) + 2 * 4 * (size_t)b_bytes(ld) + (2 * kRing + 9) * 8 + 64 + 2 * 8 * 4 +
+         2 * 32 * 4;
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads, so
+// that a decision to leave a loop is the same in every one of them.
+__device__ __forceinline__ bool named_sync_or(int id, int count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(out)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
+    const __nv_bfloat16* __restrict__ dig, const int32_t* __restrict__ row_exp, const int32_t* __restrict__ remap0,
+    int32_t n_dom, int N, int nrhs, Levels al, const double* __restrict__ r, int64_t stride,
+    const double* __restrict__ zl, int64_t lstride, double* __restrict__ z, int* __restrict__ flags) {
+  using namespace umma;
+  extern __shared__ unsigned char smem_raw[];
+  const int ld = 3 * N;
+  const uint32_t sbytes = slot_bytes(ld), bb = b_bytes(ld);
+  const uint32_t dig_bytes = (uint32_t)ld * ld * 2;
+  unsigned char* ring = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char* sBbuf = ring + kRing * sbytes;  // [2][4 pair operands]
+  uint64_t* full = (uint64_t*)(sBbuf + 2 * 4 * bb);
+  uint64_t* empty = full + kRing;
+  uint64_t* bfull = empty + kRing;  // [2]
+  uint64_t* bempty = bfull + 2;     // [2]
+  uint64_t* tfull = bempty + 2;     // [2]
+  uint64_t* tempty = tfull + 2;     // [2]
+  uint64_t* drain = tempty + 2;     // [1]
+  uint32_t* tslot = (uint32_t*)(drain + 1);
+  volatile int* abort_word = (volatile int*)(tslot + 1);
+  int* sexp = (int*)(tslot + 16);  // [2][8]
+  int* snode = sexp + 16;          // [2][32]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_local = n_dom > (int)blockIdx.x ? (n_dom - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kRing; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bfull[b], 1);
+      mbar_init(&bempty[b], 2);  // the MMAs (commit) and the epilogue
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 1);
+    }
+    mbar_init(drain, 1);
+    *abort_word = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, 256);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int seq = 0;
+      for (int n = 0; n < n_local && !*abort_word; ++n) {
+        const __nv_bfloat16* dd = dig + (int64_t)(blockIdx.x + (int64_t)n * gridDim.x) * kDigits * ld * ld;
+        for (int p = 0; p < kDigits; ++p) {
+          const int slot = seq % kRing, use = seq / kRing;
+          if (use > 0 && !mbar_wait(&empty[slot], (uint32_t)(use - 1) & 1u)) {
+            *abort_word = 1;
+            atomicOr(flags, kErrTimeout);
+          }
+          if (*abort_word) break;
+          mbar_arrive_expect_tx(&full[slot], dig_bytes);
+          bulk_g2s(ring + slot * sbytes, dd + (int64_t)p * ld * ld, dig_bytes, &full[slot]);
+          ++seq;
+        }
+      }
+      // every copy issued lands before the CTA can leave (the last use of each slot)
+      for (int s = 0; s < kRing && s < seq; ++s) mbar_wait(&full[s], (uint32_t)((seq - 1 - s) / kRing) & 1u);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t lbo = (uint32_t)ld * 16;
+      const uint32_t idesc = idesc_bf16_f32(kM, 16);
+      const uint64_t da0 = smem_desc(smem_u32(ring), lbo, 128);
+      const uint64_t db0 = smem_desc(smem_u32(sBbuf), 256, 128);
+      const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 512u >> 4, db_j = bb >> 4, db_buf = (4u * bb) >> 4;
+      int seq = 0;
+      bool issued = false;
+      for (int n = 0; n < n_local && !*abort_word; ++n) {
+        const int b = n & 1, use = n >> 1;
+        bool ok = (use == 0 || mbar_wait(&tempty[b], (uint32_t)(use - 1) & 1u)) &&
+                  mbar_wait(&bfull[b], (uint32_t)use & 1u);
+        if (ok) {
+          fence_after_sync();
+          const uint32_t tbase = tmem + 128u * b;
+          for (int p = 0; p < kDigits && ok; ++p, ++seq) {
+            const int slot = seq % kRing;
+            if (!mbar_wait(&full[slot], (uint32_t)(seq / kRing) & 1u)) {
+              ok = false;
+              break;
+            }
+            fence_after_sync();
+            const uint64_t da = da0 + ((uint64_t)slot * sbytes >> 4);
+            for (int j = 0; j < pairs_for(p); ++j) {
+              const uint32_t dcol = tbase + 8u * (p + 2 * j);
+              const uint64_t db = db0 + b * db_buf + j * db_j;
+#pragma unroll 6
+              for (int ks = 0; ks < ld / 16; ++ks)
+                mma_bf16(dcol, da + ks * da_ks, db + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[slot]);
+            issued = true;
+          }
+        }
+        if (!ok) {
+          *abort_word = 1;
+          atomicOr(flags, kErrTimeout);
+          break;
+        }
+        mma_commit(&tfull[b]);
+        mma_commit(&bempty[b]);
+      }
+      if (issued) {  // every MMA issued finishes before TMEM can be released
+        mma_commit(drain);
+        mbar_wait(drain, 0);
+      }
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ stagers (64 threads)
+    const int st = tid - 64;
+    for (int n = 0; n < n_local; ++n) {
+      const int b = n & 1, use = n >> 1;
+      const int32_t d = blockIdx.x + n * gridDim.x;
+      bool bad = *abort_word != 0;
+      if (!bad && use > 0 && !mbar_wait(&bempty[b], (uint32_t)(use - 1) & 1u)) {
+        bad = true;
+        *abort_word = 1;
+        atomicOr(flags, kErrTimeout);
+      }
+      if (named_sync_or(1, 64, bad)) break;
+      int* se = sexp + 8 * b;
+      int* sn = snode + 32 * b;
+      if (st < 8) se[st] = 0;
+      if (st < 32) sn[st] = st < N ? remap0[(int64_t)d * N + st] : -1;
+      named_sync(1, 64);
+      constexpr int kSPer = 8 * 128 / 64;
+      double rv[kSPer];
+#pragma unroll
+      for (int m = 0; m < kSPer; ++m) {
+        const int e = st + m * 64;
+        const int k = e / ld, j = e - k * ld;
+        rv[m] = 0.0;
+        if (k < nrhs && k < 8) {
+          const int32_t node = sn[j / 3];
+          if (node >= 0) rv[m] = r[k * stride + 3 * (int64_t)node + j % 3];
+          if (rv[m] != 0.0) atomicMax(&se[k], biased_exp(rv[m]));
+        }
+      }
+      named_sync(1, 64);
+      unsigned char* sB = sBbuf + b * 4 * bb;
+#pragma unroll
+      for (int m = 0; m < kSPer; ++m) {
+        const int e = st + m * 64;
+        if (e >= 8 * ld) break;
+        const int k = e / ld, j = e - k * ld;
+        const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], se[k] - 1021) : 0;
+        int dg[kDigits];
+        digits(y, dg);
+        unsigned char* col = sB + (j >> 3) * 256 + (j & 7) * 2 + k * 16;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *(__nv_bfloat16*)(col + (q >> 1) * bb + (q & 1) * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
+      }
+      fence_proxy_async();
+      named_sync(1, 64);
+      if (st == 0) mbar_arrive(&bfull[b]);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (128 threads)
+    const int q4 = warp & 3;  // TMEM lane quarter
+    const int i_row = q4 * 32 + lane;
+    for (int n = 0; n < n_local; ++n) {
+      const int b = n & 1, use = n >> 1;
+      const int32_t d = blockIdx.x + n * gridDim.x;
+      bool bad = *abort_word != 0;
+      if (!bad && !mbar_wait(&bfull[b], (uint32_t)use & 1u)) {  // this domain's node map and exponents
+        bad = true;
+        *abort_word = 1;
+        atomicOr(flags, kErrTimeout);
+      }
+      if (named_sync_or(2, 128, bad)) break;
+      const int* se = sexp + 8 * b;
+      const int32_t node = i_row < ld ? snode[32 * b + i_row / 3] : -1;
+      int a = -100000;
+      double coarse_sum[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) coarse_sum[k] = 0.0;
+      const int c = i_row % 3;
+      if (node >= 0) {
+        a = row_exp[(int64_t)d * ld + i_row];
+#pragma unroll
+        for (int l = 1; l < 8; ++l) {
+          if (l >= al.L) break;
+          const int64_t item = al.vec_off[l] + al.coarse[l][node];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (k < nrhs) coarse_sum[k] += zl[k * lstride + 3 * item + c];
+        }
+      }
+      bad = !mbar_wait(&tfull[b], (uint32_t)use & 1u);
+      if (bad) {
+        *abort_word = 1;
+        atomicOr(flags, kErrTimeout);
+      }
+      if (named_sync_or(2, 128, bad)) break;
+      fence_after_sync();
+      if (q4 * 32 < ld) {
+        const uint32_t ta = tmem + 128u * b + ((uint32_t)(q4 * 32) << 16);
+        float g[64];
+        tmem_ld_32x32b_x16(ta + 0, g);
+        tmem_ld_32x32b_x16(ta + 16, g + 16);
+        tmem_ld_32x32b_x16(ta + 32, g + 32);
+        tmem_ld_32x32b_x16(ta + 48, g + 48);
+        if (node >= 0) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (k >= nrhs) break;
+            double v = 0.0;
+            if (se[k] && a > -100000) {
+              long long hi = 0, lo = 0;
+#pragma unroll
+              for (int s = 0; s < 4; ++s) hi = (hi << 8) + (long long)__float2int_rn(g[8 * s + k]);
+#pragma unroll
+              for (int s = 4; s < 8; ++s) lo = (lo << 8) + (long long)__float2int_rn(g[8 * s + k]);
+              const int e = a + (se[k] - 1021) - 72;
+              if (e < 900) v = scaled_to_double(hi, lo, e);
+            }
+            z[k * stride + 3 * (int64_t)node + c] = v + coarse_sum[k];
+          }
+        }
+      }
+      fence_before_sync();
+      named_sync(2, 128);
+      if (tid == 128) {
+        mbar_arrive(&tempty[b]);
+        mbar_arrive(&bempty[b]);
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
 }  // namespace f64tc
 
 bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs) {
-  return mas->precision == GS_PREC_FP64 && mas->dig64 != nullptr && nrhs >= 1 && nrhs <= 8 &&
+  return mas->precision == GS_PREC_FP64 && !mas->dig64.empty() && nrhs >= 1 && nrhs <= 8 &&
          ctx->tune[GS_TUNE_F64_TC] != 0;
 }
 
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas) {
   const int ld = 3 * mas->N;
-  if (mas->precision != GS_PREC_FP64 || ld % 16 != 0 || ld > f64tc::kM || mas->dig64) return GS_OK;
-  const int64_t n_dom = mas->n_domains[0];
-  GS_TRY(ctx->alloc(&mas->dig64, (size_t)std::max<int64_t>(n_dom, 1) * f64tc::kDigits * ld * ld * 2));
-  GS_TRY(ctx->alloc((void**)&mas->dig64_exp, (size_t)std::max<int64_t>(n_dom, 1) * ld * 4));
-  if (n_dom) {
-    GS_PROF(ctx, GS_K_MAS_INVERT);
-    f64tc::k_split_inverse<<<n_dom, ((ld + 31) / 32) * 32, 0, ctx->stream>>>(
-        mas->inv64[0], ld, (__nv_bfloat16*)mas->dig64, mas->dig64_exp);
+  if (mas->precision != GS_PREC_FP64 || ld % 16 != 0 || ld > f64tc::kM || !mas->dig64.empty()) return GS_OK;
+  for (int l = 0; l < mas->L; ++l) {  // every level: level 0 and the coarse levels
+    const int64_t n_dom = mas->n_domains[l];
+    void* dg = nullptr;
+    int32_t* ex = nullptr;
+    GS_TRY(ctx->alloc(&dg, (size_t)std::max<int64_t>(n_dom, 1) * f64tc::kDigits * ld * ld * 2));
+    mas->dig64.push_back(dg);
+    GS_TRY(ctx->alloc((void**)&ex, (size_t)std::max<int64_t>(n_dom, 1) * ld * 4));
+    mas->dig64_exp.push_back(ex);
+    if (n_dom) {
+      GS_PROF(ctx, GS_K_MAS_INVERT);
+      f64tc::k_split_inverse<<<n_dom, ((ld + 31) / 32) * 32, 0, ctx->stream>>>(mas->inv64[l], ld,
+                                                                               (__nv_bfloat16*)dg, ex);
+    }
   }
+  GS_TRY(ctx->alloc((void**)&mas->d_dig_tab, 16 * sizeof(void*)));
+  std::vector<void*> hp(16, nullptr);
+  for (int l = 0; l < mas->L; ++l) hp[l] = mas->dig64[l], hp[8 + l] = mas->dig64_exp[l];
+  GS_CUDA(cudaMemcpyAsync(mas->d_dig_tab, hp.data(), 16 * sizeof(void*), cudaMemcpyHostToDevice, ctx->stream));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
+}
+
+static f64tc::Levels f64tc_levels(gs_mas mas) {
+  f64tc::Levels al{};
+  al.L = mas->L;
+  for (int l = 0; l < mas->L; ++l) al.coarse[l] = mas->coarse[l], al.vec_off[l] = mas->vec_off[l];
+  return al;
 }
 
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
                         int64_t lstride, double* z) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
   if (mas->n_domains[0] == 0) return GS_OK;
-  const int ld = 3 * mas->N;
-  f64tc::Levels al{};
-  al.L = mas->L;
-  for (int l = 0; l < mas->L; ++l) al.coarse[l] = mas->coarse[l], al.vec_off[l] = mas->vec_off[l];
-  const size_t smem = f64tc::smem_bytes(ld);
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  f64tc::k_level0_f64tc<<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
-      (const __nv_bfloat16*)mas->dig64, mas->dig64_exp, mas->remap0, mas->N, nrhs, al, r, stride, zl, lstride, z,
+  if (ctx->tune[GS_TUNE_F64_TC] == 2) {  // persistent, warp-specialised: one CTA per SM
+    const size_t psmem = f64tc::psmem_bytes(3 * mas->N);
+    GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)psmem));
+    const int grid = std::min<int>(mas->n_domains[0], std::max(ctx->sm_count, 1));
+    f64tc::k_level0_f64tc_persistent<<<grid, f64tc::kPThreads, psmem, ctx->stream>>>(
+        (const __nv_bfloat16*)mas->dig64[0], mas->dig64_exp[0], mas->remap0, mas->n_domains[0], mas->N, nrhs,
+        f64tc_levels(mas), r, stride, zl, lstride, z, ctx->d_flags);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  }
+  const size_t smem = f64tc::smem_bytes(3 * mas->N);
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
+  const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
+  f64tc::k_level0_f64tc<false><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
+      tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,
       ctx->d_flags);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride) {
+  GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
+  if (mas->n_coarse_jobs == 0) return GS_OK;
+  const size_t smem = f64tc::smem_bytes(3 * mas->N);
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
+  const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
+  f64tc::k_level0_f64tc<true><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(
+      tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,
+      f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags);
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

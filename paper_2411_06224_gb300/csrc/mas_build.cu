@@ -389,8 +389,9 @@ int gs_mas_destroy(gs_mas mas) {
   for (auto p : mas->inv32) c->release(p);
   for (auto p : mas->inv16) c->release(p);
   c->release(mas->inv16_tc);
-  c->release(mas->dig64);
-  c->release(mas->dig64_exp);
+  for (auto p : mas->dig64) c->release(p);
+  for (auto p : mas->dig64_exp) c->release(p);
+  c->release(mas->d_dig_tab);
   c->release(mas->remap0);
   c->release(mas->d_inv_tab);
   c->release(mas->d_coarse_jobs);
