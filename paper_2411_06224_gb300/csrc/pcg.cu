@@ -131,12 +131,16 @@ __device__ void finalize(PcgScalars* s, double* __restrict__ partials, double my
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int k = 0; k < nrhs; ++k) {
+  // one warp per right-hand side (fixed order: lane, then stride 32, then
+  // the shuffle tree), so the tail costs one warp reduction, not nrhs block ones
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = w; k < nrhs; k += kRedThreads / 32) {
     double v = 0.0;
-    for (int g = threadIdx.x; g < (int)gridDim.x; g += blockDim.x) v += __ldcg(&partials[k * kMaxRedBlocks + g]);
-    const double sum = block_sum(v);
-    if (threadIdx.x == 0) apply_op(s, k, sum, op, tol2);
+    for (int g = lane; g < (int)gridDim.x; g += 32) v += __ldcg(&partials[k * kMaxRedBlocks + g]);
+    v = warp_sum(v);
+    if (lane == 0) apply_op(s, k, v, op, tol2);
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int all = 1;
     for (int k = 0; k < nrhs; ++k) all &= s->conv[k] != 0;
