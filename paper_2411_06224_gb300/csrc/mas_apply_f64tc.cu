@@ -13,9 +13,11 @@
 //   * apply: column k of r_d gets b_k with |r_jk| < 2^(b_k-1), likewise
 //     Y_jk = rint(r_jk 2^(56-b_k)) -> digits n^(1..7);
 //   * G_s = sum_{p+q=s} m^(p) n^(q) for s = 2..9 (products of digits <= 2^14,
-//     96 terms, <= 7 pairs: |G_s| < 2^24, exact in FP32): the tensor core
-//     accumulates each G_s in its own 8 TMEM columns, one MMA per (digit p,
-//     pair of digits q, q+1) with N = 16;
+//     96 terms, <= 7 pairs: |G_s| < 2^24, exact in FP32): the B operand holds
+//     all 7 digit columns of r (plus a zero one, N = 64), so one MMA per digit
+//     matrix and K step writes the groups p+2 .. p+9 into TMEM columns
+//     8p .. 8p+63; each G_s collects in its own 8 columns (groups above 9 are
+//     not read);
 //   * z_ik = 2^(a_i + b_k - 72) sum_{s=2..9} G_s 256^(9-s), combined in
 //     64-bit integers (two halves) and rounded once to a double in integer
 //     arithmetic, so the epilogue spends one FP64 add (the coarse levels).
@@ -144,9 +146,6 @@ __global__ void k_split_inverse(const double* __restrict__ inv, int ld, __nv_bfl
   }
 }
 
-// digit p (0-based) times digit pair j -> TMEM column 8 * (p + 2 j): the
-// groups s = p + 2j + 2 and s + 1 (1-based digits p+1 and 2j+1, 2j+2)
-__device__ __forceinline__ int pairs_for(int p) { return (8 - (p + 1)) / 2 + 1; }
 
 // kCoarse = false: level 0, CTA = level-0 domain, r gathered through remap0,
 //   z = level-0 product + prolongated coarse results, written per node;
@@ -232,10 +231,10 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], sexp[k] - 1021) : 0;
     int dg[kDigits];
     digits(y, dg);
-    unsigned char* col = sB + (j >> 3) * 256 + (j & 7) * 2 + k * 16;
+    unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)  // q = 7: the missing 8th digit, zero
-      *(__nv_bfloat16*)(col + (q >> 1) * bb + (q & 1) * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
+    for (int q = 0; q < 8; ++q)  // column n = 8 q + k; q = 7: the missing 8th digit, zero
+      *(__nv_bfloat16*)(col + q * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
   }
   fence_proxy_async();
   __syncthreads();
@@ -271,10 +270,10 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     int loads[kSlots];  // copies issued into each slot
     for (int s = 0; s < kSlots; ++s) loads[s] = 1;
     const uint32_t lbo = (uint32_t)ld * 16;
-    const uint32_t idesc = idesc_bf16_f32(kM, 16);
+    const uint32_t idesc = idesc_bf16_f32(kM, 64);
     const uint64_t da0 = smem_desc(smem_u32(ring), lbo, 128);
-    const uint64_t db0 = smem_desc(smem_u32(sB), 256, 128);
-    const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 512u >> 4, db_j = bb >> 4;
+    const uint64_t db0 = smem_desc(smem_u32(sB), 1024, 128);
+    const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 2048u >> 4;
     for (int p = 0; p < kDigits && ok; ++p) {
       const int slot = p % kSlots;
       if (!mbar_wait(&full[slot], (uint32_t)(p / kSlots) & 1u)) {
@@ -283,13 +282,11 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
       }
       fence_after_sync();
       const uint64_t da = da0 + ((uint64_t)slot * sbytes >> 4);
-      for (int j = 0; j < pairs_for(p); ++j) {
-        const uint32_t dcol = tmem + 8u * (p + 2 * j);
-        const uint64_t db = db0 + j * db_j;
+      // digit p times all digit columns of r: groups s = p + 2 .. p + 9 at TMEM
+      // columns 8 p .. 8 p + 63 (group s at column 8 (s - 2))
 #pragma unroll 6
-        for (int ks = 0; ks < ld / 16; ++ks)
-          mma_bf16(dcol, da + ks * da_ks, db + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
-      }
+      for (int ks = 0; ks < ld / 16; ++ks)
+        mma_bf16(tmem + 8u * p, da + ks * da_ks, db0 + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
       mma_commit(&empty[slot]);
       const int q = p - 1;  // the previous digit's slot takes digit q + kSlots
       if (q >= 0 && q + kSlots < kDigits) {
@@ -472,10 +469,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t lbo = (uint32_t)ld * 16;
-      const uint32_t idesc = idesc_bf16_f32(kM, 16);
+      const uint32_t idesc = idesc_bf16_f32(kM, 64);
       const uint64_t da0 = smem_desc(smem_u32(ring), lbo, 128);
-      const uint64_t db0 = smem_desc(smem_u32(sBbuf), 256, 128);
-      const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 512u >> 4, db_j = bb >> 4, db_buf = (4u * bb) >> 4;
+      const uint64_t db0 = smem_desc(smem_u32(sBbuf), 1024, 128);
+      const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 2048u >> 4, db_buf = (4u * bb) >> 4;
       int seq = 0;
       bool issued = false;
       for (int n = 0; n < n_local && !*abort_word; ++n) {
@@ -493,13 +490,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
             }
             fence_after_sync();
             const uint64_t da = da0 + ((uint64_t)slot * sbytes >> 4);
-            for (int j = 0; j < pairs_for(p); ++j) {
-              const uint32_t dcol = tbase + 8u * (p + 2 * j);
-              const uint64_t db = db0 + b * db_buf + j * db_j;
+            const uint64_t db = db0 + b * db_buf;
 #pragma unroll 6
-              for (int ks = 0; ks < ld / 16; ++ks)
-                mma_bf16(dcol, da + ks * da_ks, db + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
-            }
+            for (int ks = 0; ks < ld / 16; ++ks)
+              mma_bf16(tbase + 8u * p, da + ks * da_ks, db + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
             mma_commit(&empty[slot]);
             issued = true;
           }
@@ -558,10 +552,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
         const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], se[k] - 1021) : 0;
         int dg[kDigits];
         digits(y, dg);
-        unsigned char* col = sB + (j >> 3) * 256 + (j & 7) * 2 + k * 16;
+        unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *(__nv_bfloat16*)(col + (q >> 1) * bb + (q & 1) * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
+        for (int q = 0; q < 8; ++q)  // column n = 8 q + k; q = 7: the missing 8th digit, zero
+          *(__nv_bfloat16*)(col + q * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
       }
       fence_proxy_async();
       named_sync(1, 64);
