@@ -280,7 +280,7 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 /* Launch shapes a context uses, set by the autotuner (or by hand).  Values
  * outside the listed set return GS_ERR_INVALID.  Results do not depend on
  * the choice except through the order of floating-point sums. */
-#define GS_TUNE_SPMV_LANES 0      /* lanes per block row of the FP64 row SpMV: 2 (default), 4, 8 */
+#define GS_TUNE_SPMV_LANES 0      /* lanes per block row of the FP64 row SpMV: 1, 2 (default), 4, 8 */
 #define GS_TUNE_SPMV32_LANES 1    /* lanes per block row of the FP32 SpMV of the mixed solve: 2 (default), 4 */
 #define GS_TUNE_APPLY_RHS 2       /* right-hand sides per thread in the level-0 MAS product: 2, 4 (default), 8 */
 #define GS_TUNE_BATCH_CHUNK 3     /* vector entries per work item of the batched reductions: 1024..16384 (4096) */

@@ -25,7 +25,7 @@ import torch
 from . import binding as B
 
 CANDIDATES = {
-    B.GS_TUNE_SPMV_LANES: (2, 4, 8),
+    B.GS_TUNE_SPMV_LANES: (1, 2, 4, 8),
     B.GS_TUNE_APPLY_RHS: (2, 4, 8),
     B.GS_TUNE_SPMV32_LANES: (2, 4),
     B.GS_TUNE_BATCH_CHUNK: (1024, 2048, 4096, 8192, 16384),

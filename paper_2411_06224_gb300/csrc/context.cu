@@ -193,7 +193,7 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
   GS_CHECK(ctx, GS_ERR_INVALID, "gs_tune_set: null context");
   bool ok = false;
   switch (param) {
-    case GS_TUNE_SPMV_LANES: ok = value == 2 || value == 4 || value == 8; break;
+    case GS_TUNE_SPMV_LANES: ok = value == 1 || value == 2 || value == 4 || value == 8; break;
     case GS_TUNE_SPMV32_LANES: ok = value == 2 || value == 4; break;
     case GS_TUNE_APPLY_RHS: ok = value == 2 || value == 4 || value == 8; break;
     case GS_TUNE_BATCH_CHUNK: ok = value >= 1024 && value <= 16384 && (value & (value - 1)) == 0; break;

@@ -262,10 +262,12 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
     if (nrhs == 1) {
       if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
     } else {
       if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 4><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
     }
 #undef GS_ROW_ARGS
