@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--batch-steps", type=int, default=2, help="timed steps of the batched form (64 uneven systems)")
     p.add_argument("--cloth", type=int, default=512,
                    help="vertices per edge of the stiff-cloth precision case (0 = skip)")
+    p.add_argument("--set-tune", action="append", default=[], metavar="NAME=VALUE",
+                   help="force a launch shape after tuning (names as in config.launch_shapes), e.g. "
+                        "spmv_lanes=2; repeatable")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--micro", action="store_true",
                    help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
@@ -313,6 +316,14 @@ def main():
         for c in lane_ctx:  # every lane uses the tuned shapes
             for prm in autotune.CANDIDATES:
                 B.gs_tune_set(c, prm, B.gs_tune_get(ctx, prm))
+    if args.set_tune:  # forced shapes, on every context
+        from paper_2411_06224_gb300 import autotune
+
+        by_name = {v: k for k, v in autotune.NAMES.items()}
+        for item in args.set_tune:
+            name, value = item.split("=")
+            for c in {id(c): c for c in [ctx] + lane_ctx}.values():
+                B.gs_tune_set(c, by_name[name], int(value))
 
     # warm-up
     for _ in range(args.warmup):

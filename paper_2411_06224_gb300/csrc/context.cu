@@ -207,7 +207,7 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
 }
 
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value) {
-  GS_CHECK(ctx && value && param >= 0 && param < 6, GS_ERR_INVALID, "gs_tune_get: bad argument");
+  GS_CHECK(ctx && value && param >= 0 && param < GS_TUNE_COUNT, GS_ERR_INVALID, "gs_tune_get: bad argument");
   *value = ctx->tune[param];
   return GS_OK;
 }

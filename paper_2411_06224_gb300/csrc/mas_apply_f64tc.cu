@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
         rv[m] = r[k * lstride + cbase + j];
       else if (node >= 0)
         rv[m] = r[k * stride + 3 * (int64_t)node + j % 3];
-      if (rv[m] != 0.0) atomicMax(&sexp[k], biased_exp(rv[m]));
+      const int eb = biased_exp(rv[m]);  // integer test: no FP64 compare
+      if (eb) atomicMax(&sexp[k], eb);
     }
   }
   __syncthreads();
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     const int e = tid + m * kThreads;
     if (e >= 8 * ld) break;
     const int k = e / ld, j = e - k * ld;
-    const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], sexp[k] - 1021) : 0;
+    const long long y = scaled_rint(rv[m], sexp[k] - 1021);  // 0 for zero entries
     int dg[kDigits];
     digits(y, dg);
     unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
@@ -258,13 +259,17 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
       const int64_t item = al.vec_off[l] + al.coarse[l][node_row];
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (k < nrhs) coarse_sum[k] += zl[k * lstride + 3 * item + c];
+        if (k < nrhs) {  // the first coarse level assigns: one FP64 add fewer per output
+          const double v = zl[k * lstride + 3 * item + c];
+          coarse_sum[k] = l == 1 ? v : coarse_sum[k] + v;
+        }
     }
   }
-  // MMA issue and ring refills (one thread).  A slot is refilled one digit
-  // later than its MMAs were issued, so the tensor core is not waited on.
-  // Descriptors are built once; their 14-bit address fields are advanced by
-  // adding byte offsets / 16 (all addresses stay below 256 KB).
+  // MMA issue and ring refills (one thread).  A slot is refilled as soon as
+  // the MMAs reading it have completed (a wait of a few hundred cycles, while
+  // the next digit's copy is still in flight), so two copies stay in flight
+  // per CTA.  Descriptors are built once; their 14-bit address fields are
+  // advanced by adding byte offsets / 16 (all addresses stay below 256 KB).
   if (tid == 0) {
     bool ok = true;
     int loads[kSlots];  // copies issued into each slot
@@ -287,17 +292,15 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
 #pragma unroll 6
       for (int ks = 0; ks < ld / 16; ++ks)
         mma_bf16(tmem + 8u * p, da + ks * da_ks, db0 + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
-      mma_commit(&empty[slot]);
-      const int q = p - 1;  // the previous digit's slot takes digit q + kSlots
-      if (q >= 0 && q + kSlots < kDigits) {
-        const int qs = q % kSlots;
-        if (!mbar_wait(&empty[qs], (uint32_t)(q / kSlots) & 1u)) {
+      if (p + kSlots < kDigits) {  // this slot takes digit p + kSlots once its MMAs are done
+        mma_commit(&empty[slot]);
+        if (!mbar_wait(&empty[slot], (uint32_t)(p / kSlots) & 1u)) {
           ok = false;
           break;
         }
-        mbar_arrive_expect_tx(&full[qs], dig_bytes);
-        bulk_g2s(ring + qs * sbytes, dd + (int64_t)(q + kSlots) * ld * ld, dig_bytes, &full[qs]);
-        ++loads[qs];
+        mbar_arrive_expect_tx(&full[slot], dig_bytes);
+        bulk_g2s(ring + slot * sbytes, dd + (int64_t)(p + kSlots) * ld * ld, dig_bytes, &full[slot]);
+        ++loads[slot];
       }
     }
     if (ok) {
@@ -539,7 +542,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
         if (k < nrhs && k < 8) {
           const int32_t node = sn[j / 3];
           if (node >= 0) rv[m] = r[k * stride + 3 * (int64_t)node + j % 3];
-          if (rv[m] != 0.0) atomicMax(&se[k], biased_exp(rv[m]));
+          const int eb = biased_exp(rv[m]);
+          if (eb) atomicMax(&se[k], eb);
         }
       }
       named_sync(1, 64);
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
         const int e = st + m * 64;
         if (e >= 8 * ld) break;
         const int k = e / ld, j = e - k * ld;
-        const long long y = (rv[m] != 0.0) ? scaled_rint(rv[m], se[k] - 1021) : 0;
+        const long long y = scaled_rint(rv[m], se[k] - 1021);
         int dg[kDigits];
         digits(y, dg);
         unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
@@ -590,7 +594,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
           const int64_t item = al.vec_off[l] + al.coarse[l][node];
 #pragma unroll
           for (int k = 0; k < 8; ++k)
-            if (k < nrhs) coarse_sum[k] += zl[k * lstride + 3 * item + c];
+            if (k < nrhs) {  // the first coarse level assigns: one FP64 add fewer per output
+          const double v = zl[k * lstride + 3 * item + c];
+          coarse_sum[k] = l == 1 ? v : coarse_sum[k] + v;
+        }
         }
       }
       bad = !mbar_wait(&tfull[b], (uint32_t)use & 1u);

@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
   __shared__ int s_lane[32];
   __shared__ int s_k;
   __shared__ int s_bad;
+  __shared__ double s_rdiag;  // 1 / L_pp of the current Cholesky step
   const int job = blockIdx.x;
   const int l = dom_level[job];
   const int d = dom_index[job];
@@ -302,7 +303,10 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
     sA[i * S + j] = M[(int64_t)gi * ld + gj];
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle
+  // right-looking Cholesky, lower triangle.  FP64 is the scarce unit: one
+  // reciprocal per step (not one per thread), and the trailing update walks
+  // only the lower triangle (a warp per row, lanes along it).
+  const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
   for (int p = 0; p < n3; ++p) {
     if (tid == 0) {
       double dpp = sA[p * S + p];
@@ -310,17 +314,18 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
         s_bad = 1;
         dpp = 1.0;
       }
-      sA[p * S + p] = sqrt(dpp);
+      const double lpp = sqrt(dpp);
+      sA[p * S + p] = lpp;
+      s_rdiag = 1.0 / lpp;
     }
     __syncthreads();
     if (s_bad) break;
-    const double inv = 1.0 / sA[p * S + p];
+    const double inv = s_rdiag;
     for (int i = p + 1 + tid; i < n3; i += T) sA[i * S + p] *= inv;
     __syncthreads();
-    const int m = n3 - p - 1;
-    for (int e = tid; e < m * m; e += T) {
-      int i = p + 1 + e / m, j = p + 1 + e % m;
-      if (j <= i) sA[i * S + j] -= sA[i * S + p] * sA[j * S + p];
+    for (int i = p + 1 + wid; i < n3; i += nw) {
+      const double lip = sA[i * S + p];
+      for (int j = p + 1 + lane; j <= i; j += 32) sA[i * S + j] -= lip * sA[j * S + p];
     }
     __syncthreads();
   }
@@ -328,19 +333,21 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
     if (tid == 0) atomicOr(flags, kErrNotSPD);
     return;
   }
-  // W = L^{-1} in place, column by column from the last
+  // W = L^{-1} in place.  The diagonal first becomes 1 / L_jj (= W_jj), then
+  // W_ij = -(sum_{q=j+1..i} W_iq L_qj) W_jj, column by column from the last.
+  for (int j = tid; j < n3; j += T) sA[j * S + j] = 1.0 / sA[j * S + j];
+  __syncthreads();
   for (int j = n3 - 1; j >= 0; --j) {
-    const double ljj = sA[j * S + j];
+    const double wjj = sA[j * S + j];
     double w = 0.0;
     const int i = j + 1 + tid;
     if (i < n3) {
       double acc = 0.0;
       for (int q = j + 1; q <= i; ++q) acc += sA[i * S + q] * sA[q * S + j];
-      w = -acc / ljj;
+      w = -acc * wjj;
     }
     __syncthreads();
     if (i < n3) sA[i * S + j] = w;
-    if (tid == 0) sA[j * S + j] = 1.0 / ljj;
     __syncthreads();
   }
   // level 0, low-precision form: keep the factor W = L^{-1} (M^{-1} = W^T W)
@@ -353,14 +360,17 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
       F[(int64_t)gi * ld + gj] = sA[i * S + j];
     }
   }
-  // inverse = W^T W, written over the real part of the global matrix
+  // inverse = W^T W, written over the real part of the global matrix; entry
+  // (i, j) and (j, i) are the same sum in the same order, so the lower
+  // triangle is computed and mirrored
   for (int e = tid; e < n3 * n3; e += T) {
     int i = e / n3, j = e % n3;
-    int lo = i > j ? i : j;
+    if (j > i) continue;
     double acc = 0.0;
-    for (int q = lo; q < n3; ++q) acc += sA[q * S + i] * sA[q * S + j];
+    for (int q = i; q < n3; ++q) acc += sA[q * S + i] * sA[q * S + j];
     int gi = 3 * s_lane[i / 3] + i % 3, gj = 3 * s_lane[j / 3] + j % 3;
     M[(int64_t)gi * ld + gj] = acc;
+    M[(int64_t)gj * ld + gi] = acc;
   }
 }
 

@@ -38,6 +38,18 @@ def test_header_declares_entry_points():
         assert n in names
 
 
+def test_binding_constants_match_the_header():
+    """Every integer GS_* macro of the header has the same value in the binding."""
+    from paper_2411_06224_gb300 import binding
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    macros = dict(re.findall(r"#define\s+(GS_[A-Z0-9_]+)\s+(\(?-?\d+\)?)", text))
+    assert len(macros) > 20
+    for name, value in macros.items():
+        assert hasattr(binding, name), name
+        assert getattr(binding, name) == int(value.strip("()")), name
+
+
 def test_library_exports_every_declared_symbol(B):
     names = declared()
     L = ctypes.CDLL(B.LIB_PATH)

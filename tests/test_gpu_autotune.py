@@ -52,7 +52,7 @@ def build(B, ctx, s, N=16, L=3, node_off=None):
 def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
-                       (B.GS_TUNE_F64_TC, 3), (7, 2)):
+                       (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
             B.gs_tune_set(ctx, param, bad)
     from paper_2411_06224_gb300 import autotune
