@@ -290,7 +290,11 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
                                      accuracy): 1 (default) one CTA per domain, 2 one persistent warp-
                                      specialised CTA per SM for level 0; 0 on the FP64 cores.  Needs 3N a
                                      multiple of 16 and nrhs <= 8 */
-#define GS_TUNE_COUNT 6           /* number of parameters */
+#define GS_TUNE_SPMV_WINDOW 6     /* row order of the row SpMVs: longest rows first within windows of this
+                                     many consecutive rows (256..65536, a power of 2; default 1024), so that
+                                     the rows in flight stay neighbours and their gathers hit L2; 0: over
+                                     all rows */
+#define GS_TUNE_COUNT 7           /* number of parameters */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
 

@@ -80,7 +80,7 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1};  // GS_TUNE_* launch shapes
+  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024};  // GS_TUNE_* launch shapes
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // device error word
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
@@ -167,6 +167,7 @@ struct gs_mat_s {
   int32_t* lo_idx = nullptr;  // nnzb - n_diag
   int32_t* lo_col = nullptr;  // the c of each such block
   int32_t* row_order = nullptr;  // rows by descending entry count (row-gather SpMV)
+  int32_t row_order_window = -1;  // GS_TUNE_SPMV_WINDOW it was built for
   int32_t* key_of_input = nullptr;  // per input block: index of the stored block it was summed into, -1 if dropped
   int64_t n_input = 0;
   float* au32 = nullptr;      // FP32 copy of au for the mixed-precision solve (built lazily)

@@ -25,7 +25,7 @@ namespace gs {
 int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant);
 int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl);
 int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl);
-int ensure_lower(gs_ctx ctx, gs_mat m);
+int ensure_row_order(gs_ctx ctx, gs_mat m);
 
 constexpr int kMaxRhs = 32;
 constexpr int kRedThreads = 256;
@@ -243,7 +243,7 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   double *rl, *zl;
   GS_TRY(mas_level_vectors(ctx, mas, nrhs, &rl, &zl));
   GS_CUDA(cudaMemsetAsync(s, 0, sizeof(PcgScalars), st));
-  if (variant == GS_SPMV_ROW) GS_TRY(ensure_lower(ctx, mat));  // built once per matrix
+  if (variant == GS_SPMV_ROW) GS_TRY(ensure_row_order(ctx, mat));  // built once per matrix
 
   const double tol2 = tol * tol;
   const dim3 vg(red_blocks(len), nrhs);

@@ -27,7 +27,7 @@ namespace gs {
 int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant);
 int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl);
 int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl);
-int ensure_lower(gs_ctx ctx, gs_mat m);
+int ensure_row_order(gs_ctx ctx, gs_mat m);
 
 namespace batch {
 
@@ -254,7 +254,7 @@ extern "C" int gs_pcg_solve_batch(gs_ctx ctx, gs_mat mat, gs_mas mas, int32_t n_
   GS_CUDA(cudaMemcpyAsync(d_wend, w_end.data(), W * 8, cudaMemcpyHostToDevice, st));
   GS_CUDA(cudaMemcpyAsync(d_wstart, w_start.data(), (n_sys + 1) * 4, cudaMemcpyHostToDevice, st));
   GS_CUDA(cudaMemsetAsync(h, 0, sizeof(Head), st));
-  GS_TRY(ensure_lower(ctx, mat));
+  GS_TRY(ensure_row_order(ctx, mat));
   double *rl, *zl;
   GS_TRY(mas_level_vectors(ctx, mas, 1, &rl, &zl));
   const double tol2 = tol * tol;

@@ -27,7 +27,7 @@
 namespace gs {
 
 int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant);
-int ensure_lower(gs_ctx ctx, gs_mat m);
+int ensure_row_order(gs_ctx ctx, gs_mat m);
 
 namespace mixed {
 
@@ -515,7 +515,7 @@ static int solve_mixed(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int 
   cudaStream_t st = ctx->stream;
   const int32_t n = mat->n;
   const int64_t len64 = 3LL * n;
-  GS_TRY(ensure_lower(ctx, mat));
+  GS_TRY(ensure_row_order(ctx, mat));
   float* au32 = nullptr;
   std::vector<float*> inv;
   GS_TRY(ensure_f32(ctx, mat, mas, &au32, inv));

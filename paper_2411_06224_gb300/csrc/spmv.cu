@@ -174,13 +174,17 @@ __global__ void k_lower_fill(const uint32_t* __restrict__ skey, const uint32_t* 
 }
 
 // Sort key of each row for the row order: entries counted from the longest
-// possible, so an ascending radix sort lists long rows first.
+// possible, so an ascending (stable) radix sort lists long rows first.
+// shift < 0: one global order.  Otherwise rows are ordered by window
+// (r >> shift) first and by length only inside it: the warps still see rows
+// of equal length, and the rows in flight stay neighbours in the mesh, so
+// their x gathers and transposed blocks hit L2.
 __global__ void k_row_len_keys(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ lo_ptr, int32_t n,
-                               uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+                               int shift, uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
   int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint32_t len = (uint32_t)(row_ptr[r + 1] - row_ptr[r] + lo_ptr[r + 1] - lo_ptr[r]);
-  key[r] = 0xffffffffu - len;
+  key[r] = shift < 0 ? 0xffffffffu - len : ((uint32_t)(r >> shift) << 16) | (0xffffu - min(len, 0xffffu));
   val[r] = (uint32_t)r;
 }
 
@@ -226,14 +230,33 @@ int ensure_lower(gs_ctx ctx, gs_mat m) {
   { GS_PROF(ctx, GS_K_OTHER); k_lower_fill<<<ceil_div(n_off + 1, 256), 256, 0, st>>>(k_out, v_out, m->rid, n_off, m->n, m->lo_ptr, m->lo_idx,
                                                          m->lo_col); }
   GS_CUDA(cudaGetLastError());
-  // row order: by total entries, longest first, ties by row index
-  GS_TRY(ctx->alloc((void**)&m->row_order, (size_t)std::max(m->n, 1) * 4));
+  return GS_OK;
+}
+
+// Row order of the row-gather SpMV for the context's window
+// (GS_TUNE_SPMV_WINDOW): by total entries, longest first, ties by row index,
+// inside windows of consecutive rows (0: over all rows).  Rebuilt when the
+// window changes.
+int ensure_row_order(gs_ctx ctx, gs_mat m) {
+  GS_TRY(ensure_lower(ctx, m));
+  const int window = ctx->tune[GS_TUNE_SPMV_WINDOW];
+  if (m->row_order && m->row_order_window == window) return GS_OK;
+  cudaStream_t st = ctx->stream;
+  int shift = -1;
+  if (window > 0) {
+    int bits = 0;  // rows need bits - 16 bits of window index above the 16 length bits
+    while (bits < 31 && (1LL << bits) < (int64_t)m->n) ++bits;
+    shift = 0;
+    while ((1 << shift) < window) ++shift;
+    shift = std::max(shift, bits - 16);
+  }
+  if (!m->row_order) GS_TRY(ctx->alloc((void**)&m->row_order, (size_t)std::max(m->n, 1) * 4));
   {
     uint32_t *lk_in, *lk_out, *lv_in;
     GS_TRY(ctx->scratch_buf(kSlotSortKeysIn, (size_t)m->n * 4 + 16, (void**)&lk_in));
     GS_TRY(ctx->scratch_buf(kSlotSortKeysOut, (size_t)m->n * 4 + 16, (void**)&lk_out));
     GS_TRY(ctx->scratch_buf(kSlotSortValsIn, (size_t)m->n * 4 + 16, (void**)&lv_in));
-    { GS_PROF(ctx, GS_K_OTHER); k_row_len_keys<<<ceil_div(m->n, 256), 256, 0, st>>>(m->row_ptr, m->lo_ptr, m->n, lk_in, lv_in); }
+    { GS_PROF(ctx, GS_K_OTHER); k_row_len_keys<<<ceil_div(m->n, 256), 256, 0, st>>>(m->row_ptr, m->lo_ptr, m->n, shift, lk_in, lv_in); }
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tb, lk_in, lk_out, lv_in, (uint32_t*)m->row_order, m->n, 0, 32, st);
     void* temp;
@@ -241,6 +264,7 @@ int ensure_lower(gs_ctx ctx, gs_mat m) {
     { GS_PROF(ctx, GS_K_LIBPRIM); GS_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, lk_in, lk_out, lv_in, (uint32_t*)m->row_order, m->n, 0, 32, st)); }
   }
   GS_CUDA(cudaGetLastError());
+  m->row_order_window = window;
   return GS_OK;
 }
 
@@ -253,7 +277,7 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
     if (m->nnzb > 0)
       { GS_PROF(ctx, GS_K_SPMV); k_spmv_srbk<4><<<ceil_div(m->nnzb, 256), 256, 0, st>>>(m->rid, m->cid, m->au, m->nnzb, stride, nrhs, x, y); }
   } else {
-    GS_TRY(ensure_lower(ctx, m));
+    GS_TRY(ensure_row_order(ctx, m));
     // lanes per block row (GS_TUNE_SPMV_LANES); 8 lanes keep 4 RHS per pass
     const int lanes = ctx->tune[GS_TUNE_SPMV_LANES];
     const int64_t threads = (int64_t)m->n * lanes;

@@ -52,13 +52,15 @@ def build(B, ctx, s, N=16, L=3, node_off=None):
 def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
-                       (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_COUNT, 2)):
+                       (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
+                       (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
             B.gs_tune_set(ctx, param, bad)
     from paper_2411_06224_gb300 import autotune
 
     assert autotune.current(ctx) == {"spmv_lanes": 2, "apply_rhs_per_thread": 4, "spmv32_lanes": 2,
-                                     "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1}
+                                     "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1,
+                                     "spmv_row_window": 1024}
 
 
 def test_every_shape_gives_the_oracle_result(B, ctx):
@@ -75,10 +77,20 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
     y = torch.empty_like(xd)
     Ax = np.stack([A(v) for v in x])
     bound = 1e-13 * np.stack([Absa(np.abs(v)) for v in x])
-    for lanes in autotune.CANDIDATES[B.GS_TUNE_SPMV_LANES]:
-        B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, lanes)
-        B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs)
-        assert np.all(np.abs(y.cpu().numpy() - Ax) <= bound), lanes
+    by_lanes = {}
+    for window in autotune.CANDIDATES[B.GS_TUNE_SPMV_WINDOW]:
+        B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WINDOW, window)
+        for lanes in autotune.CANDIDATES[B.GS_TUNE_SPMV_LANES]:
+            B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, lanes)
+            B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs)
+            assert np.all(np.abs(y.cpu().numpy() - Ax) <= bound), (window, lanes)
+            # the row order only decides which thread takes a row, not the
+            # order of the row's sum: bitwise the same for every window
+            if lanes in by_lanes:
+                assert torch.equal(y, by_lanes[lanes]), (window, lanes)
+            else:
+                by_lanes[lanes] = y.clone()
+    B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WINDOW, 1024)
     zs = {}
     B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 0)  # the RHS-per-thread shape belongs to the FP64-core kernel
     for rpt in autotune.CANDIDATES[B.GS_TUNE_APPLY_RHS]:
