@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
     p.add_argument("--no-lanes", dest="lanes", action="store_false",
                    help="solve the systems of a step one after another on one stream")
+    p.add_argument("--step-sync", dest="queue", action="store_false",
+                   help="with lanes: wait for all systems of a step before the next step starts, instead of one "
+                        "queue over the timed steps' solves")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default launch shapes instead of tuning them first")
     p.add_argument("--batch-steps", type=int, default=2, help="timed steps of the batched form (64 uneven systems)")
@@ -246,7 +249,10 @@ def main():
     n_lanes = len(dsys) if args.lanes else 1
     lane_streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)] if args.lanes else [stream]
     lane_ctx = [B.gs_create(local, s_) for s_ in lane_streams] if args.lanes else [ctx]
-    lane_x = [torch.zeros_like(b) for _ in range(n_lanes)] if args.lanes else [x]
+    # solution buffers per lane and system: two steps' solves of one system
+    # may run at once on two lanes
+    lane_xs = [[torch.zeros_like(b) for _ in dsys] for _ in range(n_lanes)] if args.lanes else [[x] * len(dsys)]
+    last_lane = {}  # system -> lane of its latest finished solve
     pool = ThreadPoolExecutor(max_workers=n_lanes)
 
     def fork():
@@ -270,12 +276,45 @@ def main():
         if n_lanes == 1:
             return [solve_one(s["rows"], s["cols"], s["blocks"], b, x) for s in dsys]
         fork()
-        futs = [pool.submit(lane_run, i, lambda i, s=s: solve_one(s["rows"], s["cols"], s["blocks"], b, lane_x[i],
+        futs = [pool.submit(lane_run, i, lambda i, s=s: solve_one(s["rows"], s["cols"], s["blocks"], b, lane_xs[i][i],
                                                                    lane_ctx[i]))
                 for i, s in enumerate(dsys)]
         out = [f.result() for f in futs]
         join()
+        for i in range(len(dsys)):
+            last_lane[i] = i
         return out
+
+    def queue(n_steps, order, job):
+        """The solves of n_steps steps as one queue over the lanes: each lane's
+        thread takes the next solve as soon as its previous one is done, so no
+        lane idles while a step's slowest system finishes.  order: the systems
+        of a step, longest first.  job(lane, system) -> result."""
+        jobs = [si for _ in range(n_steps) for si in order]
+        nxt = iter(range(len(jobs)))
+        lock = threading.Lock()
+        out = {}
+
+        def worker(i):
+            while True:
+                with lock:
+                    j = next(nxt, None)
+                if j is None:
+                    return
+                r = job(i, jobs[j])
+                with lock:
+                    out[jobs[j]] = r
+                    last_lane[jobs[j]] = i
+
+        fork()
+        futs = [pool.submit(lane_run, i, worker) for i in range(n_lanes)]
+        [f.result() for f in futs]
+        join()
+        return [out[si] for si in range(len(dsys))]
+
+    def solve_job(i, si):
+        s = dsys[si]
+        return solve_one(s["rows"], s["cols"], s["blocks"], b, lane_xs[i][si], lane_ctx[i])
 
     def profile_begin(classes):
         for c in lane_ctx:
@@ -334,6 +373,9 @@ def main():
     for _ in range(args.warmup):
         warm = step()
     iters = [[int(v) for v in o[0]] for o in warm]
+    # the queue takes a step's systems longest first (by the warm-up's iterations)
+    order = sorted(range(len(dsys)), key=lambda si: -max(iters[si]))
+    use_queue = n_lanes > 1 and args.queue
     nnzb = warm[0][2][0]
     mas_levels = warm[0][2][1]
     # per-class breakdown of one step, the systems one after another on the
@@ -354,8 +396,11 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     w0 = time.perf_counter()
     e0.record(stream)
-    for _ in range(args.steps):
-        res = step()
+    if use_queue:
+        res = queue(args.steps, order, solve_job)
+    else:
+        for _ in range(args.steps):
+            res = step()
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -370,7 +415,7 @@ def main():
     # true residuals of the last step (checked on the device through the library's SpMV)
     true_rel = []
     if n_lanes > 1:
-        x.copy_(lane_x[-1])
+        x.copy_(lane_xs[last_lane[len(dsys) - 1]][len(dsys) - 1])
     Ax = torch.empty_like(x)
     for s in dsys[-1:]:
         mat = B.gs_assemble(ctx, V, s["rows"], s["cols"], s["blocks"])
@@ -392,28 +437,32 @@ def main():
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        hxs = [torch.empty_like(hb).pin_memory() for _ in hsys]
+        hxs = [[torch.empty_like(hb).pin_memory() for _ in hsys] for _ in range(n_lanes)]
 
-        def e2e_one(i, h, c):
+        def e2e_one(i, si, c):  # lane i, system si
+            h = hsys[si]
             rows = h["rows"].to(dev, non_blocking=True)
             cols = h["cols"].to(dev, non_blocking=True)
             blocks = h["blocks"].to(dev, non_blocking=True)
             bb = hb.to(dev, non_blocking=True)
             xx = torch.empty_like(bb)
             solve_one(rows, cols, blocks, bb, xx, c)
-            hxs[i].copy_(xx, non_blocking=True)
+            hxs[i][si].copy_(xx, non_blocking=True)
             torch.cuda.current_stream().synchronize()  # the host holds the answer
 
         f0.record(stream)
-        for _ in range(args.e2e_steps):
-            if n_lanes == 1:
-                for i, h in enumerate(hsys):
-                    e2e_one(i, h, ctx)
-            else:
-                fork()
-                futs = [pool.submit(lane_run, i, lambda i, h=h: e2e_one(i, h, lane_ctx[i])) for i, h in enumerate(hsys)]
-                [f.result() for f in futs]
-                join()
+        if use_queue:
+            queue(args.e2e_steps, order, lambda i, si: e2e_one(i, si, lane_ctx[i]))
+        else:
+            for _ in range(args.e2e_steps):
+                if n_lanes == 1:
+                    for si in range(len(hsys)):
+                        e2e_one(0, si, ctx)
+                else:
+                    fork()
+                    futs = [pool.submit(lane_run, i, lambda i: e2e_one(i, i, lane_ctx[i])) for i in range(len(hsys))]
+                    [f.result() for f in futs]
+                    join()
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_rate, el = replicas.throughput(len(hsys) * args.e2e_steps, f0.elapsed_time(f1) / 1e3, dev)
@@ -701,6 +750,10 @@ def main():
             "pcg_iterations": iters, "true_rel_residual_last_system": true_rel,
             "l2": "inputs larger than L2 (1.07 GB of triplets and 0.6 GB of level-0 inverses per system vs 129 MB L2); no flush",
             "parallelism": f"independent systems per GPU x{world}",
+            "schedule": (f"one queue over the timed steps' {len(dsys)} x steps solves on {n_lanes} streams, "
+                         "each step's systems longest first" if use_queue else
+                         (f"{n_lanes} streams, one system each, synchronised per step" if n_lanes > 1
+                          else "one stream, systems one after another")),
             "launch_shapes": autotune_current(B, ctx),
             "autotune": tuned,
         },

@@ -294,7 +294,10 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
                                      many consecutive rows (256..65536, a power of 2; default 1024), so that
                                      the rows in flight stay neighbours and their gathers hit L2; 0: over
                                      all rows */
-#define GS_TUNE_COUNT 7           /* number of parameters */
+#define GS_TUNE_SPMV_WS 7         /* FP64 row SpMV: 1 (default) a persistent grid (two blocks per SM) whose
+                                     warps take the next rows of the order from a counter; 0 one thread
+                                     group per row */
+#define GS_TUNE_COUNT 8           /* number of parameters */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
 

@@ -18,6 +18,8 @@ The shapes and the kernels they steer:
   * GS_TUNE_F64_TC       FP64 apply on the BF16 tensor cores (exact digit
                          splitting; one CTA per domain or one persistent CTA
                          per SM) or on the FP64 cores;
+  * GS_TUNE_SPMV_WS      one thread group per row, or a persistent grid whose
+                         warps steal the next rows;
   * GS_TUNE_SPMV_WINDOW  rows per window of the SpMV's length order.  Not swept:
                          timed alone the SpMV prefers one global order (the
                          longest rows first also balance its tail), but windows
@@ -38,6 +40,7 @@ CANDIDATES = {
     B.GS_TUNE_BF16_TC: (1, 0),
     B.GS_TUNE_F64_TC: (1, 2, 0),
     B.GS_TUNE_SPMV_WINDOW: (0, 256, 1024, 4096, 16384),
+    B.GS_TUNE_SPMV_WS: (0, 1),
 }
 
 NAMES = {
@@ -48,6 +51,7 @@ NAMES = {
     B.GS_TUNE_BF16_TC: "bf16_tensor_cores",
     B.GS_TUNE_F64_TC: "fp64_on_tensor_cores",
     B.GS_TUNE_SPMV_WINDOW: "spmv_row_window",
+    B.GS_TUNE_SPMV_WS: "spmv_work_stealing",
 }
 
 
@@ -98,8 +102,10 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     x = torch.randn((nrhs, 3 * n), dtype=torch.float64, device="cuda", generator=gen)
     y = torch.empty_like(x)
     out = {}
-    out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(
-        ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs), reps)
+    spmv = lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs)
+    sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
+    out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, spmv, reps)
+    out[NAMES[B.GS_TUNE_SPMV_WS]] = sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
     apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
     if fp64:
         out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps)

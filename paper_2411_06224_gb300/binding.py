@@ -48,7 +48,8 @@ GS_TUNE_BATCH_CHUNK = 3
 GS_TUNE_BF16_TC = 4
 GS_TUNE_F64_TC = 5
 GS_TUNE_SPMV_WINDOW = 6
-GS_TUNE_COUNT = 7
+GS_TUNE_SPMV_WS = 7
+GS_TUNE_COUNT = 8
 
 K_NAMES = ["assemble", "libprim", "spmv", "mas_levels", "mas_matrices", "mas_invert", "mas_apply_l0",
            "mas_apply_coarse", "pcg_vector", "other"]

@@ -50,6 +50,10 @@ enum : int {
 
 int status_from_flags(int flags);
 
+// Word of the context's 256-byte device flag area that counts the chunks
+// taken by the work-stealing SpMV (zeroed before each launch).
+constexpr int kSpmvCounterWord = 16;
+
 // ------------------------------------------------------------------ memory
 // A grow-only device buffer from the stream-ordered pool.
 struct Buffer {
@@ -80,9 +84,9 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024};  // GS_TUNE_* launch shapes
+  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024, 1};  // GS_TUNE_* launch shapes
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
-  int* d_flags = nullptr;     // device error word
+  int* d_flags = nullptr;     // 256 device bytes: [0] error word, [kSpmvCounterWord] SpMV work counter
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
   std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls
 

@@ -25,9 +25,10 @@
 // row and column maxima, the level of FP64's own rounding.
 //
 // One CTA per domain, 128 threads; the 7 digit matrices (18 KB each) stream
-// through a 2-slot shared-memory ring filled by bulk asynchronous copies
-// (50 KB per CTA), so four CTAs share an SM and hide each other's latency.  All
-// waits are bounded (kErrTimeout); TMEM is always freed.
+// through a shared-memory ring filled by bulk asynchronous copies: 2 slots at
+// level 0 (50 KB per CTA, four CTAs share an SM and hide each other's
+// latency), 4 for the few coarse-level domains.  All waits are bounded
+// (kErrTimeout); TMEM is always freed.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,7 +40,9 @@ namespace gs {
 namespace f64tc {
 
 constexpr int kDigits = 7;
-constexpr int kSlots = 2;
+constexpr int kSlots = 2;        // ring slots of the level-0 kernel (4 CTAs per SM; 3 slots and
+                                 // 3 CTAs per SM measured 15 % slower)
+constexpr int kSlotsCoarse = 4;  // coarse levels: few CTAs, so a deeper ring per CTA
 constexpr int kThreads = 128;
 constexpr int kM = 128;
 constexpr int kTmemCols = 128;  // groups s = 2..10, 8 columns each (72 used)
@@ -54,8 +57,9 @@ __host__ __device__ inline uint32_t slot_bytes(int ld) {  // K-major M = 128 spa
   return ((uint32_t)(ld * ld * 2 - ld * 16 + kM * 16) + 127u) & ~127u;
 }
 __host__ __device__ inline uint32_t b_bytes(int ld) { return (uint32_t)(ld / 8) * 256; }
+template <int kS>
 __host__ inline size_t smem_bytes(int ld) {
-  return 128 + (size_t)kSlots * slot_bytes(ld) + 4 * (size_t)b_bytes(ld) + (2 * kSlots + 1) * 8 + 8 + 8 * 4 + 32 * 4;
+  return 128 + (size_t)kS * slot_bytes(ld) + 4 * (size_t)b_bytes(ld) + (2 * kS + 1) * 8 + 8 + 8 * 4 + 32 * 4;
 }
 
 // T 2^e as the nearest double (ties to even), T = hi 2^32 + lo with
@@ -151,7 +155,7 @@ __global__ void k_split_inverse(const double* __restrict__ inv, int ld, __nv_bfl
 //   z = level-0 product + prolongated coarse results, written per node;
 // kCoarse = true: one coarse-level domain per CTA (job tables), r and z are the
 //   level's contiguous multilevel vectors rl, zl.
-template <bool kCoarse>
+template <bool kCoarse, int kS>
 __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* const* __restrict__ dig_tab,
                                                            const int32_t* const* __restrict__ exp_tab,
                                                            const int32_t* __restrict__ job_level,
@@ -166,10 +170,10 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   const uint32_t sbytes = slot_bytes(ld), bb = b_bytes(ld);
   const uint32_t dig_bytes = (uint32_t)ld * ld * 2;
   unsigned char* ring = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char* sB = ring + kSlots * sbytes;  // 4 pair operands [n^(2j+1) | n^(2j+2)]
+  unsigned char* sB = ring + kS * sbytes;  // 4 pair operands [n^(2j+1) | n^(2j+2)]
   uint64_t* full = (uint64_t*)(sB + 4 * bb);
-  uint64_t* empty = full + kSlots;
-  uint64_t* done = empty + kSlots;
+  uint64_t* empty = full + kS;
+  uint64_t* done = empty + kS;
   uint32_t* tslot = (uint32_t*)(done + 1);
   int* sfail = (int*)(tslot + 1);
   int* sexp = sfail + 1;   // [8] biased exponent maxima of the RHS columns
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   const int64_t cbase = kCoarse ? 3 * (al.vec_off[lvl] + (int64_t)d * N) : 0;  // coarse: first entry of the domain
 
   if (tid == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], 1);
+    for (int s = 0; s < kS; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], 1);
     mbar_init(done, 1);
     *sfail = 0;
     fence_mbar_init();
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   fence_after_sync();
   const uint32_t tmem = *tslot;
   if (tid == 0) {
-    for (int p = 0; p < kSlots; ++p) {
+    for (int p = 0; p < kS; ++p) {
       mbar_arrive_expect_tx(&full[p], dig_bytes);
       bulk_g2s(ring + p * sbytes, dd + (int64_t)p * ld * ld, dig_bytes, &full[p]);
     }
@@ -272,16 +276,16 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   // advanced by adding byte offsets / 16 (all addresses stay below 256 KB).
   if (tid == 0) {
     bool ok = true;
-    int loads[kSlots];  // copies issued into each slot
-    for (int s = 0; s < kSlots; ++s) loads[s] = 1;
+    int loads[kS];  // copies issued into each slot
+    for (int s = 0; s < kS; ++s) loads[s] = 1;
     const uint32_t lbo = (uint32_t)ld * 16;
     const uint32_t idesc = idesc_bf16_f32(kM, 64);
     const uint64_t da0 = smem_desc(smem_u32(ring), lbo, 128);
     const uint64_t db0 = smem_desc(smem_u32(sB), 1024, 128);
     const uint64_t da_ks = (2u * lbo) >> 4, db_ks = 2048u >> 4;
     for (int p = 0; p < kDigits && ok; ++p) {
-      const int slot = p % kSlots;
-      if (!mbar_wait(&full[slot], (uint32_t)(p / kSlots) & 1u)) {
+      const int slot = p % kS;
+      if (!mbar_wait(&full[slot], (uint32_t)(p / kS) & 1u)) {
         ok = false;
         break;
       }
@@ -292,14 +296,14 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
 #pragma unroll 6
       for (int ks = 0; ks < ld / 16; ++ks)
         mma_bf16(tmem + 8u * p, da + ks * da_ks, db0 + ks * db_ks, idesc, (p > 0 || ks > 0) ? 1u : 0u);
-      if (p + kSlots < kDigits) {  // this slot takes digit p + kSlots once its MMAs are done
+      if (p + kS < kDigits) {  // this slot takes digit p + kS once its MMAs are done
         mma_commit(&empty[slot]);
-        if (!mbar_wait(&empty[slot], (uint32_t)(p / kSlots) & 1u)) {
+        if (!mbar_wait(&empty[slot], (uint32_t)(p / kS) & 1u)) {
           ok = false;
           break;
         }
         mbar_arrive_expect_tx(&full[slot], dig_bytes);
-        bulk_g2s(ring + slot * sbytes, dd + (int64_t)(p + kSlots) * ld * ld, dig_bytes, &full[slot]);
+        bulk_g2s(ring + slot * sbytes, dd + (int64_t)(p + kS) * ld * ld, dig_bytes, &full[slot]);
         ++loads[slot];
       }
     }
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     } else {
       *sfail = 1;
       atomicOr(flags, kErrTimeout);
-      for (int s = 0; s < kSlots; ++s)  // let the last copy into each slot land before the CTA leaves
+      for (int s = 0; s < kS; ++s)  // let the last copy into each slot land before the CTA leaves
         mbar_wait(&full[s], (uint32_t)(loads[s] - 1) & 1u);
       mbar_arrive(done);
     }
@@ -702,12 +706,12 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   }
-  const size_t smem = f64tc::smem_bytes(3 * mas->N);
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
-  f64tc::k_level0_f64tc<false><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
+  const size_t smem = f64tc::smem_bytes<f64tc::kSlots>(3 * mas->N);
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false, f64tc::kSlots>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  f64tc::k_level0_f64tc<false, f64tc::kSlots><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
       tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,
       ctx->d_flags);
   GS_CUDA(cudaGetLastError());
@@ -717,12 +721,14 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
 int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
   if (mas->n_coarse_jobs == 0) return GS_OK;
-  const size_t smem = f64tc::smem_bytes(3 * mas->N);
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  // a few hundred coarse domains at most: a deeper ring per CTA shortens the
+  // chain of copy latencies that bounds this small launch
+  const size_t smem = f64tc::smem_bytes<f64tc::kSlotsCoarse>(3 * mas->N);
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
-  f64tc::k_level0_f64tc<true><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(
+  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(
       tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,
       f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags);
   GS_CUDA(cudaGetLastError());

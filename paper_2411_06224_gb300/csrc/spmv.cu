@@ -15,6 +15,8 @@
 // per right-hand side against 80 bytes per block read once for all RHS).
 #include <cub/device/device_radix_sort.cuh>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "primitives.cuh"
 
@@ -75,15 +77,15 @@ __global__ void __launch_bounds__(256) k_spmv_srbk(const int32_t* __restrict__ r
 // kLanes lanes per block row; each lane strides over the row's entries
 // (its upper blocks first, then its transposed references) and keeps kR
 // right-hand sides in registers, so every block is loaded once per kR RHS.
+// One thread group's share of the product: thread t of the walk over the
+// row order (kLanes threads per row).
 template <int kLanes, int kR>
-__global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_order,
-                                                  const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
-                                                  const int32_t* __restrict__ lo_ptr,
-                                                  const int32_t* __restrict__ lo_idx,
-                                                  const int32_t* __restrict__ lo_col, const double* __restrict__ au,
-                                                  int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
-                                                  double* __restrict__ y) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void spmv_row_group(int64_t t, const int32_t* __restrict__ row_order,
+                                               const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
+                                               const int32_t* __restrict__ lo_ptr, const int32_t* __restrict__ lo_idx,
+                                               const int32_t* __restrict__ lo_col, const double* __restrict__ au,
+                                               int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
+                                               double* __restrict__ y) {
   const int32_t slot = (int32_t)(t / kLanes);
   int sub = threadIdx.x % kLanes;
   bool in = slot < n;
@@ -147,6 +149,43 @@ __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ ro
           yr[0] = acc[3 * q + 0], yr[1] = acc[3 * q + 1], yr[2] = acc[3 * q + 2];
         }
     }
+  }
+}
+
+template <int kLanes, int kR>
+__global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ row_order,
+                                                  const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
+                                                  const int32_t* __restrict__ lo_ptr,
+                                                  const int32_t* __restrict__ lo_idx,
+                                                  const int32_t* __restrict__ lo_col, const double* __restrict__ au,
+                                                  int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
+                                                  double* __restrict__ y) {
+  spmv_row_group<kLanes, kR>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, row_order, row_ptr, cid, lo_ptr, lo_idx,
+                             lo_col, au, n, stride, nrhs, x, y);
+}
+
+// Work-stealing form (GS_TUNE_SPMV_WS): a persistent grid whose warps take
+// the next 32 threads' worth of rows of the row order from a counter, so the
+// rows in flight stay one contiguous stretch of the order and no SM idles in
+// a tail of long rows.  Capped at the one-pass kernel's 88 registers, so two
+// blocks per SM leave the same room to other streams' kernels.
+template <int kLanes, int kR>
+__global__ void __maxnreg__(88) k_spmv_row_ws(const int32_t* __restrict__ row_order,
+                                              const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cid,
+                                              const int32_t* __restrict__ lo_ptr, const int32_t* __restrict__ lo_idx,
+                                              const int32_t* __restrict__ lo_col, const double* __restrict__ au,
+                                              int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
+                                              double* __restrict__ y, int* __restrict__ counter) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunks = ((int64_t)n * kLanes + 31) / 32;
+#pragma unroll 1
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= chunks) break;  // whole warp
+    spmv_row_group<kLanes, kR>((int64_t)c * 32 + lane, row_order, row_ptr, cid, lo_ptr, lo_idx, lo_col, au, n,
+                               stride, nrhs, x, y);
   }
 }
 
@@ -283,7 +322,23 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
     const int64_t threads = (int64_t)m->n * lanes;
     const int grid = ceil_div(threads, 256);
 #define GS_ROW_ARGS m->row_order, m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col, m->au, m->n, stride, nrhs, x, y
-    if (nrhs == 1) {
+    if (ctx->tune[GS_TUNE_SPMV_WS] && ctx->sm_count > 0) {  // work stealing over a persistent grid
+      int* counter = ctx->d_flags + kSpmvCounterWord;
+      GS_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+      const int wgrid = std::min(grid, 2 * ctx->sm_count);  // 88 registers: two blocks of 256 per SM
+      GS_PROF(ctx, GS_K_SPMV);
+      if (nrhs == 1) {
+        if (lanes == 8) k_spmv_row_ws<8, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else if (lanes == 2) k_spmv_row_ws<2, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else if (lanes == 1) k_spmv_row_ws<1, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else k_spmv_row_ws<4, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+      } else {
+        if (lanes == 8) k_spmv_row_ws<8, 4><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else if (lanes == 2) k_spmv_row_ws<2, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else if (lanes == 1) k_spmv_row_ws<1, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        else k_spmv_row_ws<4, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+      }
+    } else if (nrhs == 1) {
       if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
       else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }

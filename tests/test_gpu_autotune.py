@@ -53,14 +53,14 @@ def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
                        (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
-                       (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_COUNT, 2)):
+                       (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_SPMV_WS, 2), (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
             B.gs_tune_set(ctx, param, bad)
     from paper_2411_06224_gb300 import autotune
 
     assert autotune.current(ctx) == {"spmv_lanes": 2, "apply_rhs_per_thread": 4, "spmv32_lanes": 2,
                                      "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1,
-                                     "spmv_row_window": 1024}
+                                     "spmv_row_window": 1024, "spmv_work_stealing": 1}
 
 
 def test_every_shape_gives_the_oracle_result(B, ctx):
@@ -80,17 +80,20 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
     by_lanes = {}
     for window in autotune.CANDIDATES[B.GS_TUNE_SPMV_WINDOW]:
         B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WINDOW, window)
-        for lanes in autotune.CANDIDATES[B.GS_TUNE_SPMV_LANES]:
-            B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, lanes)
-            B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs)
-            assert np.all(np.abs(y.cpu().numpy() - Ax) <= bound), (window, lanes)
-            # the row order only decides which thread takes a row, not the
-            # order of the row's sum: bitwise the same for every window
-            if lanes in by_lanes:
-                assert torch.equal(y, by_lanes[lanes]), (window, lanes)
-            else:
-                by_lanes[lanes] = y.clone()
+        for ws in autotune.CANDIDATES[B.GS_TUNE_SPMV_WS]:
+            B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WS, ws)
+            for lanes in autotune.CANDIDATES[B.GS_TUNE_SPMV_LANES]:
+                B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, lanes)
+                B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs)
+                assert np.all(np.abs(y.cpu().numpy() - Ax) <= bound), (window, ws, lanes)
+                # the row order and the schedule only decide which thread takes a
+                # row, not the order of the row's sum: bitwise the same for all
+                if lanes in by_lanes:
+                    assert torch.equal(y, by_lanes[lanes]), (window, ws, lanes)
+                else:
+                    by_lanes[lanes] = y.clone()
     B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WINDOW, 1024)
+    B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WS, 1)
     zs = {}
     B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 0)  # the RHS-per-thread shape belongs to the FP64-core kernel
     for rpt in autotune.CANDIDATES[B.GS_TUNE_APPLY_RHS]:

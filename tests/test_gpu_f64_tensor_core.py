@@ -99,7 +99,7 @@ def test_digit_split_apply_matches_fp64(B, ctx, n, N, L, nrhs):
     z0 = mas.apply(om.levels, invs, r, om.C)
     absz = mas.apply(om.levels, [np.abs(v) for v in invs], np.abs(r), om.C)
     assert np.all(np.abs(out[0] - z0) <= 3e-14 * absz + 1e-300)  # FP64 cores: reordered FP64 sums (<= 99 terms)
-    # the two tensor-core schedules compute the same integers and round them the same
+    # the tensor-core schedules compute the same integers and round them the same
     # way; they differ only through the restriction's unordered (atomic) coarse sums
     assert np.all(np.abs(out[1] - out[2]) <= 1e-14 * absz + 1e-300)
     om.invs = invs
