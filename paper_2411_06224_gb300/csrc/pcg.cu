@@ -30,6 +30,7 @@ int ensure_row_order(gs_ctx ctx, gs_mat m);
 constexpr int kMaxRhs = 32;
 constexpr int kRedThreads = 256;
 constexpr int kMaxRedBlocks = 256;  // reduction blocks per right-hand side
+constexpr int kUnroll = 4;          // strided elements per thread and pass of k_dot and k_update_p
 
 struct PcgScalars {
   double bnorm2[kMaxRhs];
@@ -50,7 +51,10 @@ enum DotOp : int { kOpBnorm = 0, kOpRzInit, kOpPAp, kOpRR, kOpRz };
 // chunk of right-hand side k.  G depends only on the vector length, so the
 // reduction order -- and therefore the result -- is fixed.
 inline int red_blocks(int64_t len) {
-  int64_t g = (len + kRedThreads * 8 - 1) / (kRedThreads * 8);
+  // 32 entries per thread: each block's reduction, fence and arrival are
+  // fixed costs, so blocks are made long (measured: 8 per thread left k_dot
+  // stalled on its block reductions at 21 % of the DRAM peak)
+  int64_t g = (len + kRedThreads * 32 - 1) / (kRedThreads * 32);
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
 
@@ -157,11 +161,26 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const double* __restrict__ 
   const int64_t o = (int64_t)blockIdx.y * len;
   int64_t i0, i1;
   chunk_of(len, i0, i1);
+  // kUnroll strided elements per pass, loaded before they are summed: more
+  // loads in flight per thread, and the thread's sum keeps its order
   double v = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const double bb = b[o + i];
-    v += a[o + i] * bb;
-    if (kCopy) dst[o + i] = bb;
+  const int64_t T = blockDim.x;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kUnroll * T) {
+    double av[kUnroll], bv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t j = i + u * T;
+      av[u] = j < i1 ? a[o + j] : 0.0;
+      bv[u] = j < i1 ? b[o + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t j = i + u * T;
+      if (j < i1) {
+        v += av[u] * bv[u];
+        if (kCopy) dst[o + j] = bv[u];
+      }
+    }
   }
   finalize(s, partials, block_sum(v), nrhs, op, 0.0);
 }
@@ -213,7 +232,19 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(double* __restrict__ p
   const int64_t o = (int64_t)k * len;
   int64_t i0, i1;
   chunk_of(len, i0, i1);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) p[o + i] = z[o + i] + be * p[o + i];
+  const int64_t T = blockDim.x;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kUnroll * T) {
+    double zv[kUnroll], pv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t j = i + u * T;
+      zv[u] = j < i1 ? z[o + j] : 0.0;
+      pv[u] = j < i1 ? p[o + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (i + u * T < i1) p[o + i + u * T] = zv[u] + be * pv[u];
+  }
 }
 
 }  // namespace gs
