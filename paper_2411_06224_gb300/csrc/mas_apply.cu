@@ -25,19 +25,19 @@ struct ApplyLevels {
   int N;
 };
 
-// One warp per level-0 domain, four warps per block.  The 24 values (8 RHS x
-// 3) of each node go through a padded shared tile so that lane q < 24 sums
-// value q over the nodes of a group: about 31 FP64 adds per group instead
-// of the 24 x 5 of shuffle trees (FP64 adds are scarce on this part).
-// Groups are the domain's level-1 items; a level-1 item lies inside one
-// item of every coarser level, so its sums serve all levels.
+// One warp per level-0 domain, four warps per block; lane q < 24 owns value q
+// of a node (RHS k0 + q / 3, component q % 3) and sums it over the nodes of
+// a group in ascending slot order: about 31 FP64 adds per group, no shuffle
+// trees (FP64 adds are scarce on this part).  Groups are the domain's level-1
+// items; a level-1 item lies inside one item of every coarser level, so its
+// sums serve all levels.  Most domains are one group: then the 32 nodes'
+// values are loaded at once and summed in registers.
 constexpr int kRestrictWarps = 4;
 
 __global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(const double* __restrict__ r, int64_t stride,
                                                                   int nrhs, const int32_t* __restrict__ remap0,
                                                                   int32_t n_dom0, ApplyLevels al,
                                                                   double* __restrict__ rl, int64_t lstride) {
-  __shared__ double tile[kRestrictWarps][32][25];
   const int wib = threadIdx.x >> 5;
   const int32_t d = (int32_t)(blockIdx.x * kRestrictWarps + wib);
   const int lane = threadIdx.x & 31;
@@ -46,30 +46,49 @@ __global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(const double* 
   const int32_t node = lane < N ? remap0[(int64_t)d * N + lane] : -1;
   const bool real = node >= 0;
   const int32_t c1 = real ? al.coarse[1][node] : -1;
-  double(*T)[25] = tile[wib];
+  const uint32_t realm = __ballot_sync(kFull, real);
+  if (!realm) return;  // whole warp
+  const int lead0 = __ffs(realm) - 1;
+  const int32_t c_first = __shfl_sync(kFull, c1, lead0);
+  const bool one_group = __all_sync(kFull, !real || c1 == c_first);
   for (int k0 = 0; k0 < nrhs; k0 += 8) {
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      const int k = k0 + q / 3;
-      T[lane][q] = (real && k < nrhs) ? r[k * stride + 3 * (int64_t)node + q % 3] : 0.0;
-    }
-    __syncwarp();
-    uint32_t left = __ballot_sync(kFull, real);
+    const int k = k0 + lane / 3, c = lane % 3;
+    const bool act = lane < 24 && k < nrhs;
+    const double* rk = r + k * stride + c;
+    uint32_t left = realm;
     while (left) {
-      const int lead = __ffs(left) - 1;
-      const int32_t cc = __shfl_sync(kFull, c1, lead);
-      const int32_t lead_node = __shfl_sync(kFull, node, lead);
-      const uint32_t g = __ballot_sync(kFull, real && c1 == cc);
+      int lead;
+      int32_t cc;
+      uint32_t g;
+      double sum = 0.0;
+      if (one_group) {  // all real slots: loads first, then the sum in slot order
+        lead = lead0, cc = c_first, g = realm;
+        double v[32];
+#pragma unroll
+        for (int s = 0; s < 32; ++s) {
+          const int32_t ns = __shfl_sync(kFull, node, s);
+          v[s] = (act && ns >= 0) ? rk[3 * (int64_t)ns] : 0.0;
+        }
+#pragma unroll
+        for (int s = 0; s < 32; ++s)
+          if ((realm >> s) & 1u) sum += v[s];
+      } else {
+        lead = __ffs(left) - 1;
+        cc = __shfl_sync(kFull, c1, lead);
+        g = __ballot_sync(kFull, real && c1 == cc);
+        for (uint32_t m = g; m; m &= m - 1) {
+          const int32_t ns = __shfl_sync(kFull, node, __ffs(m) - 1);
+          if (act) sum += rk[3 * (int64_t)ns];
+        }
+      }
       left &= ~g;
-      if (lane < 24 && k0 + lane / 3 < nrhs) {
-        double sum = 0.0;
-        for (uint32_t m = g; m; m &= m - 1) sum += T[__ffs(m) - 1][lane];
-        const int64_t o = (k0 + lane / 3) * lstride + lane % 3;
+      const int32_t lead_node = __shfl_sync(kFull, node, lead);
+      if (act) {
+        const int64_t o = k * lstride + c;
         atomicAdd(&rl[o + 3 * (al.vec_off[1] + cc)], sum);
         for (int l = 2; l < al.L; ++l) atomicAdd(&rl[o + 3 * (al.vec_off[l] + al.coarse[l][lead_node])], sum);
       }
     }
-    __syncwarp();
   }
 }
 
