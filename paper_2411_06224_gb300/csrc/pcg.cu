@@ -48,13 +48,19 @@ struct PcgScalars {
 enum DotOp : int { kOpBnorm = 0, kOpRzInit, kOpPAp, kOpRR, kOpRz };
 
 // Grid of the vector kernels: (G, nrhs); block (g, k) covers a contiguous
-// chunk of right-hand side k.  G depends only on the vector length, so the
-// reduction order -- and therefore the result -- is fixed.
-inline int red_blocks(int64_t len) {
+// chunk of right-hand side k.  G depends only on the vector length, the RHS
+// count and the GPU's SM count, so on one GPU the reduction order -- and
+// therefore the result -- is fixed.
+inline int red_blocks(int64_t len, int nrhs, int sms) {
   // 32 entries per thread: each block's reduction, fence and arrival are
   // fixed costs, so blocks are made long (measured: 8 per thread left k_dot
-  // stalled on its block reductions at 21 % of the DRAM peak)
+  // stalled on its block reductions at 21 % of the DRAM peak) -- but no
+  // fewer than about two blocks per SM over all RHS while a block still gets
+  // 8 entries per thread
   int64_t g = (len + kRedThreads * 32 - 1) / (kRedThreads * 32);
+  const int64_t want = (2LL * std::max(sms, 1) + nrhs - 1) / nrhs;
+  const int64_t cap8 = (len + kRedThreads * 8 - 1) / (kRedThreads * 8);
+  g = std::max(g, std::min(want, cap8));
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, kMaxRedBlocks));
 }
 
@@ -277,7 +283,7 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   if (variant == GS_SPMV_ROW) GS_TRY(ensure_row_order(ctx, mat));  // built once per matrix
 
   const double tol2 = tol * tol;
-  const dim3 vg(red_blocks(len), nrhs);
+  const dim3 vg(red_blocks(len, nrhs, ctx->sm_count), nrhs);
   { GS_PROF(ctx, GS_K_PCG_VECTOR); k_init<<<vg, kRedThreads, 0, st>>>(b, x, r, len, nrhs, s, partials); }
   GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
   { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<true><<<vg, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit); }
