@@ -41,10 +41,10 @@ APPLY_DRAM_BYTES_PER_DOMAIN_8RHS = 172.9e6 / 2000
 # from the ncu capture on the 64^3 case (profiles/k_level0_f64tc_tet48.md):
 # 1,115.9 MB read + 48.4 MB written over 8,192 domains
 F64TC_DRAM_BYTES_PER_DOMAIN_8RHS = (1115.9e6 + 48.4e6) / 8192
-# DRAM bytes of one row-SpMV launch on the 64^3 sweep system at 8 RHS, 1 lane
-# per row and the 1024-row order window, from the same capture
-# (profiles/k_spmv_row_fp64_tet64.md): 357.1 MB read + 69.1 MB written
-SPMV_DRAM_BYTES_64 = 357.1e6 + 69.1e6
+# DRAM bytes of one work-stealing row-SpMV launch on the 64^3 sweep system at
+# 8 RHS and the 1024-row order window, by lanes per row, from ncu captures
+# (profiles/k_spmv_row_fp64_tet64.md)
+SPMV_WS_DRAM_BYTES_64 = {1: 426.5e6 + 75.6e6, 2: 225.2e6 + 39.8e6}
 TOL = 1e-6
 METRIC = "Newton solves/s to 1e-6 rel. residual (FP64 MAS-PCG)"
 
@@ -712,11 +712,12 @@ def main():
         apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
         apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
                                 "(level-0 MAS apply + prolongation)")
-    spmv_traffic = (SPMV_DRAM_BYTES_64 if args.grid == 64 and args.nrhs == 8 and args.spmv == "row"
-                    and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_LANES) == 1
-                    and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WINDOW) == 1024 else None)  # the captured shape
+    spmv_ws = args.spmv == "row" and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WS) == 1
+    spmv_traffic = (SPMV_WS_DRAM_BYTES_64.get(B.gs_tune_get(ctx, B.GS_TUNE_SPMV_LANES))
+                    if spmv_ws and args.grid == 64 and args.nrhs == 8
+                    and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WINDOW) == 1024 else None)  # the captured shapes
     spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, spmv_traffic)
-    spmv_line["kernel"] = f"k_spmv_{args.spmv}"
+    spmv_line["kernel"] = "k_spmv_row_ws" if spmv_ws else f"k_spmv_{args.spmv}"
     # alone: the same arithmetic over the sequential step's durations
     spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
                              "achieved": spmv_flops / t_spmv_iso / 1e12,
