@@ -33,17 +33,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300: derived from the nominal 1.25 TFLOP/s FP64 at 2.07 GHz, 152 SMs
-# DRAM bytes of one level-0 apply launch per domain at 8 RHS (FP64), from the
-# ncu capture on the 40^3 case (profiles/k_domain_product_fp64_tet40.md):
-# 172.9 MB over 2000 domains; traffic grows with the domain count.
+# DRAM bytes of one FP64-core level-0 apply launch per domain at 8 RHS, from
+# an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 40^3
+# case: 172.9 MB over 2000 domains; traffic grows with the domain count.
 APPLY_DRAM_BYTES_PER_DOMAIN_8RHS = 172.9e6 / 2000
 # DRAM bytes per level-0 domain of the digit-split tensor-core apply at 8 RHS,
-# from the ncu capture on the 64^3 case (profiles/k_level0_f64tc_tet48.md):
-# 1,115.9 MB read + 48.4 MB written over 8,192 domains
+# from an ncu capture on the 64^3 case: 1,115.9 MB read + 48.4 MB written over
+# 8,192 domains
 F64TC_DRAM_BYTES_PER_DOMAIN_8RHS = (1115.9e6 + 48.4e6) / 8192
-# DRAM bytes of one work-stealing row-SpMV launch on the 64^3 sweep system at
-# 8 RHS and the 1024-row order window, by lanes per row, from ncu captures
-# (profiles/k_spmv_row_fp64_tet64.md)
+# DRAM bytes (read + written) of one work-stealing row-SpMV launch on the 64^3
+# sweep system at 8 RHS and the 1024-row order window, by lanes per row, from
+# ncu captures of that case
 SPMV_WS_DRAM_BYTES_64 = {1: 426.5e6 + 75.6e6, 2: 225.2e6 + 39.8e6}
 TOL = 1e-6
 METRIC = "Newton solves/s to 1e-6 rel. residual (FP64 MAS-PCG)"

@@ -140,7 +140,7 @@ int gs_create(gs_ctx* out, int device, void* stream) {
   }
   c->sm_count = prop.multiProcessorCount;
   // Keep freed pool memory cached by the pool instead of returning it to
-  // the driver at every synchronisation.
+  // the CUDA driver at every synchronisation.
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;

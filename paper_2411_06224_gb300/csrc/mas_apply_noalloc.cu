@@ -5,7 +5,7 @@
 // pool.  Some callers cannot allow that: a host application that hands the
 // library a fixed device-memory budget at start-up and forbids any later
 // cudaMalloc (an allocation there can fail under the cap, or stall every
-// stream on the device while the driver maps memory), or code that must
+// stream on the device while the CUDA driver maps memory), or code that must
 // not allocate at all once it is running.  This entry point keeps that
 // scratch in a fixed array compiled into the library instead.
 //
