@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
     p.add_argument("--no-lanes", dest="lanes", action="store_false",
                    help="solve the systems of a step one after another on one stream")
+    p.add_argument("--streams", type=int, default=0,
+                   help="with lanes: library contexts / streams working the queue (0 = one per system of a step)")
     p.add_argument("--step-sync", dest="queue", action="store_false",
                    help="with lanes: wait for all systems of a step before the next step starts, instead of one "
                         "queue over the timed steps' solves")
@@ -246,7 +248,7 @@ def main():
     # default) each runs on its own library context and CUDA stream, driven by
     # its own host thread, so the FP64-pipe-bound SpMV of one system overlaps
     # the HBM- and tensor-bound MAS apply of another.
-    n_lanes = len(dsys) if args.lanes else 1
+    n_lanes = (args.streams if args.streams > 0 and args.queue else len(dsys)) if args.lanes else 1
     lane_streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)] if args.lanes else [stream]
     lane_ctx = [B.gs_create(local, s_) for s_ in lane_streams] if args.lanes else [ctx]
     # solution buffers per lane and system: two steps' solves of one system
@@ -370,8 +372,8 @@ def main():
                 B.gs_tune_set(c, by_name[name], int(value))
 
     # warm-up
-    for _ in range(args.warmup):
-        warm = step()
+    for _ in range(args.warmup):  # with the queue its own lanes, so --streams may differ from the systems
+        warm = queue(1, list(range(len(dsys))), solve_job) if (n_lanes > 1 and args.queue) else step()
     iters = [[int(v) for v in o[0]] for o in warm]
     # the queue takes a step's systems longest first (by the warm-up's iterations)
     order = sorted(range(len(dsys)), key=lambda si: -max(iters[si]))
