@@ -16,6 +16,11 @@
  *     matching *_destroy call.
  *   - All work is issued on the context's stream.  Calls that return sizes
  *     or statuses synchronise that stream before returning.
+ *   - Threads: one context per host thread at a time.  A gs_mat or gs_mas
+ *     may move between contexts but is used by one at a time: the row SpMV
+ *     builds its transposed references and row order into the matrix on
+ *     first use, and rebuilds the order when a context with another
+ *     GS_TUNE_SPMV_WINDOW uses it.
  *   - Indices are int32; block values are float64, each 3x3 block stored
  *     row-major (9 consecutive doubles).
  *   - Vectors hold 3 doubles per block row (x, y, z).  Several right-hand
