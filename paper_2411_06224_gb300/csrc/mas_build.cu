@@ -259,8 +259,13 @@ struct InvJob {
   int32_t items_in_domain;  // l >= 1: real items of this domain
 };
 
-// One CTA per domain.  Shared memory holds the compacted real part with
-// an odd row stride so column walks do not conflict on banks.
+// One CTA per domain.  Shared memory holds the lower triangle of the
+// compacted real part, packed by rows (entry (i, j), j <= i, at
+// i (i + 1) / 2 + j: 37 KB at 3k = 96, so five CTAs share an SM), plus a
+// contiguous copy of the current Cholesky column.  The arithmetic is that of
+// the full-storage form, operation for operation.
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
 __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
                                                          const int32_t* __restrict__ remap0, int32_t n_dom0,
                                                          const int32_t* __restrict__ dom_level,
@@ -268,6 +273,7 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
                                                          const int32_t* __restrict__ n_items, int N, int* flags,
                                                          double* __restrict__ fac0) {
   extern __shared__ double sA[];
+  __shared__ double colp[96];  // column p of the factor, rows p+1 ..
   __shared__ int s_lane[32];
   __shared__ int s_k;
   __shared__ int s_bad;
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
   const int ld = 3 * N;
   double* M = mats[l] + (int64_t)d * ld * ld;
   const int tid = threadIdx.x, T = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
   if (tid < 32) {
     bool real;
     if (l == 0)
@@ -294,38 +301,41 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
   __syncthreads();
   const int k = s_k;
   const int n3 = 3 * k;
-  const int S = n3 + 1;  // shared row stride
   if (k == 0) return;
-  // load the compacted real part
-  for (int e = tid; e < n3 * n3; e += T) {
-    int i = e / n3, j = e % n3;
-    int gi = 3 * s_lane[i / 3] + i % 3, gj = 3 * s_lane[j / 3] + j % 3;
-    sA[i * S + j] = M[(int64_t)gi * ld + gj];
+  // load the lower triangle of the compacted real part (a warp per row)
+  for (int i = wid; i < n3; i += nw) {
+    const int gi = 3 * s_lane[i / 3] + i % 3;
+    for (int j = lane; j <= i; j += 32) sA[tri(i, j)] = M[(int64_t)gi * ld + 3 * s_lane[j / 3] + j % 3];
   }
   __syncthreads();
   // right-looking Cholesky, lower triangle.  FP64 is the scarce unit: one
   // reciprocal per step (not one per thread), and the trailing update walks
-  // only the lower triangle (a warp per row, lanes along it).
-  const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+  // only the lower triangle (a warp per row, lanes along it, the column read
+  // from its contiguous copy).
   for (int p = 0; p < n3; ++p) {
     if (tid == 0) {
-      double dpp = sA[p * S + p];
+      double dpp = sA[tri(p, p)];
       if (!(dpp > 0.0)) {
         s_bad = 1;
         dpp = 1.0;
       }
       const double lpp = sqrt(dpp);
-      sA[p * S + p] = lpp;
+      sA[tri(p, p)] = lpp;
       s_rdiag = 1.0 / lpp;
     }
     __syncthreads();
     if (s_bad) break;
     const double inv = s_rdiag;
-    for (int i = p + 1 + tid; i < n3; i += T) sA[i * S + p] *= inv;
+    for (int i = p + 1 + tid; i < n3; i += T) {
+      const double v = sA[tri(i, p)] * inv;
+      sA[tri(i, p)] = v;
+      colp[i] = v;
+    }
     __syncthreads();
     for (int i = p + 1 + wid; i < n3; i += nw) {
-      const double lip = sA[i * S + p];
-      for (int j = p + 1 + lane; j <= i; j += 32) sA[i * S + j] -= lip * sA[j * S + p];
+      const double lip = colp[i];
+      const int ri = tri(i, 0);
+      for (int j = p + 1 + lane; j <= i; j += 32) sA[ri + j] -= lip * colp[j];
     }
     __syncthreads();
   }
@@ -335,29 +345,28 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
   }
   // W = L^{-1} in place.  The diagonal first becomes 1 / L_jj (= W_jj), then
   // W_ij = -(sum_{q=j+1..i} W_iq L_qj) W_jj, column by column from the last.
-  for (int j = tid; j < n3; j += T) sA[j * S + j] = 1.0 / sA[j * S + j];
+  for (int j = tid; j < n3; j += T) sA[tri(j, j)] = 1.0 / sA[tri(j, j)];
   __syncthreads();
   for (int j = n3 - 1; j >= 0; --j) {
-    const double wjj = sA[j * S + j];
+    const double wjj = sA[tri(j, j)];
     double w = 0.0;
     const int i = j + 1 + tid;
     if (i < n3) {
       double acc = 0.0;
-      for (int q = j + 1; q <= i; ++q) acc += sA[i * S + q] * sA[q * S + j];
+      const int ri = tri(i, 0);
+      for (int q = j + 1; q <= i; ++q) acc += sA[ri + q] * sA[tri(q, j)];
       w = -acc * wjj;
     }
     __syncthreads();
-    if (i < n3) sA[i * S + j] = w;
+    if (i < n3) sA[tri(i, j)] = w;
     __syncthreads();
   }
   // level 0, low-precision form: keep the factor W = L^{-1} (M^{-1} = W^T W)
   if (fac0 && l == 0) {
     double* F = fac0 + (int64_t)d * ld * ld;
-    for (int e = tid; e < n3 * n3; e += T) {
-      int i = e / n3, j = e % n3;
-      if (j > i) continue;
-      int gi = 3 * s_lane[i / 3] + i % 3, gj = 3 * s_lane[j / 3] + j % 3;
-      F[(int64_t)gi * ld + gj] = sA[i * S + j];
+    for (int i = wid; i < n3; i += nw) {
+      const int gi = 3 * s_lane[i / 3] + i % 3;
+      for (int j = lane; j <= i; j += 32) F[(int64_t)gi * ld + 3 * s_lane[j / 3] + j % 3] = sA[tri(i, j)];
     }
   }
   // inverse = W^T W, written over the real part of the global matrix; entry
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(256) k_invert_domains(double* const* mats,
     int i = e / n3, j = e % n3;
     if (j > i) continue;
     double acc = 0.0;
-    for (int q = i; q < n3; ++q) acc += sA[q * S + i] * sA[q * S + j];
+    for (int q = i; q < n3; ++q) acc += sA[tri(q, i)] * sA[tri(q, j)];
     int gi = 3 * s_lane[i / 3] + i % 3, gj = 3 * s_lane[j / 3] + j % 3;
     M[(int64_t)gi * ld + gj] = acc;
     M[(int64_t)gj * ld + gi] = acc;
@@ -547,7 +556,7 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
       cudaMemcpyAsync(d_items, mas->n_items.data(), L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(d_mats, hm.data(), L * sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return fail(GS_ERR_CUDA);
-  const size_t smem = (size_t)(3 * N) * (3 * N + 1) * sizeof(double);
+  const size_t smem = (size_t)(3 * N) * (3 * N + 1) / 2 * sizeof(double);  // packed lower triangle
   if (cudaFuncSetAttribute(k_invert_domains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return fail(GS_ERR_CUDA);
   // BF16 form: level 0 keeps its inverse Cholesky factors (rounding W keeps
