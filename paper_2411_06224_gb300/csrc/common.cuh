@@ -153,9 +153,15 @@ int level0_bf16_launch(gs_ctx ctx, gs_mas mas, bool f32_node_major, int nrhs, co
 // splitting (FP64 accuracy); mas_apply_f64tc.cu.
 bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas);
+// skip (device, may be null): the kernels return at once while *skip is set
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
-                        int64_t lstride, double* z);
-int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride);
+                        int64_t lstride, double* z, const int* skip = nullptr);
+int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride,
+                        const int* skip = nullptr);
+// y = A x (row or SRBK variant) and z = M^{-1} r, with the same skip word
+int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant, const int* skip);
+int mas_apply_launch_skip(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl,
+                          const int* skip);
 }  // namespace gs
 
 struct gs_mat_s {

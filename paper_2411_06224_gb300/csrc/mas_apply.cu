@@ -37,7 +37,9 @@ constexpr int kRestrictWarps = 4;
 __global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(const double* __restrict__ r, int64_t stride,
                                                                   int nrhs, const int32_t* __restrict__ remap0,
                                                                   int32_t n_dom0, ApplyLevels al,
-                                                                  double* __restrict__ rl, int64_t lstride) {
+                                                                  double* __restrict__ rl, int64_t lstride,
+                                                                  const int* __restrict__ skip) {
+  if (skip && *skip) return;  // every RHS of the solve has converged
   const int wib = threadIdx.x >> 5;
   const int32_t d = (int32_t)(blockIdx.x * kRestrictWarps + wib);
   const int lane = threadIdx.x & 31;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(256) k_coarse_product(const Ts* const* __restr
 
 template <typename Ts, typename Tm>
 static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const int32_t* d_jobs, int n_coarse_jobs,
-                        const double* r, double* z, int nrhs, double* rl, double* zl) {
+                        const double* r, double* z, int nrhs, double* rl, double* zl, const int* skip) {
   cudaStream_t st = ctx->stream;
   const int N = mas->N, ld = 3 * N;
   const int64_t stride = 3LL * mas->n;
@@ -205,10 +207,10 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
   if (mas->L > 1) {
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
     { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div(mas->n_domains[0], kRestrictWarps), 32 * kRestrictWarps, 0, st>>>(r, stride, nrhs, mas->remap0,
-                                                                              mas->n_domains[0], al, rl, lstride); }
+                                                                              mas->n_domains[0], al, rl, lstride, skip); }
     if (level0_f64tc_usable(ctx, mas, nrhs)) {  // FP64 accuracy on the BF16 tensor cores
       GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
-      GS_TRY(coarse_f64tc_launch(ctx, mas, nrhs, rl, zl, lstride));
+      GS_TRY(coarse_f64tc_launch(ctx, mas, nrhs, rl, zl, lstride, skip));
     } else {
       GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
       const int64_t outs = (int64_t)n_coarse_jobs * ld * nrhs;
@@ -221,7 +223,8 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
     GS_TRY(level0_bf16_launch(ctx, mas, false, nrhs, r, stride, zl, lstride, z, nullptr, ctx->d_flags));
   } else if (level0_f64tc_usable(ctx, mas, nrhs)) {  // FP64 accuracy on the BF16 tensor cores
     GS_PROF(ctx, GS_K_MAS_APPLY_L0);
-    GS_TRY(level0_f64tc_launch(ctx, mas, nrhs, (const double*)r, stride, (const double*)zl, lstride, (double*)z));
+    GS_TRY(level0_f64tc_launch(ctx, mas, nrhs, (const double*)r, stride, (const double*)zl, lstride, (double*)z,
+                               skip));
   } else {
     GS_PROF(ctx, GS_K_MAS_APPLY_L0);
 #define GS_L0_ARGS d_inv, d_jobs, d_jobs, N, nrhs, r, z, stride, mas->remap0, rl, zl, lstride, al
@@ -238,12 +241,19 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
 }
 
 int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl) {
+  return mas_apply_launch_skip(ctx, mas, r, z, nrhs, rl, zl, nullptr);
+}
+
+// The same, but the restriction and the digit-split products return at once
+// while *skip (device) is set (PCG's all-converged word).
+int mas_apply_launch_skip(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl,
+                          const int* skip) {
   // the BF16 form's coarse levels are FP32 inverses
   if (mas->precision == GS_PREC_FP32 || mas->precision == GS_PREC_BF16)
     return launch_apply<float, float>(ctx, mas, (const float* const*)mas->d_inv_tab, mas->d_coarse_jobs,
-                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl, skip);
   return launch_apply<double, double>(ctx, mas, (const double* const*)mas->d_inv_tab, mas->d_coarse_jobs,
-                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl);
+                                      mas->n_coarse_jobs, r, z, nrhs, rl, zl, skip);
 }
 
 int mas_level_vectors(gs_ctx ctx, gs_mas mas, int nrhs, double** rl, double** zl) {

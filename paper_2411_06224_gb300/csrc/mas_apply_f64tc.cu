@@ -163,8 +163,10 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
                                                            const int32_t* __restrict__ remap0, int N, int nrhs,
                                                            Levels al, const double* __restrict__ r, int64_t stride,
                                                            const double* __restrict__ zl, int64_t lstride,
-                                                           double* __restrict__ z, int* __restrict__ flags) {
+                                                           double* __restrict__ z, int* __restrict__ flags,
+                                                           const int* __restrict__ skip) {
   using namespace umma;
+  if (skip && *skip) return;  // whole CTA, before any barrier or TMEM use
   extern __shared__ unsigned char smem_raw[];
   const int ld = 3 * N;
   const uint32_t sbytes = slot_bytes(ld), bb = b_bytes(ld);
@@ -692,7 +694,7 @@ static f64tc::Levels f64tc_levels(gs_mas mas) {
 }
 
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
-                        int64_t lstride, double* z) {
+                        int64_t lstride, double* z, const int* skip) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
   if (mas->n_domains[0] == 0) return GS_OK;
   if (ctx->tune[GS_TUNE_F64_TC] == 2) {  // persistent, warp-specialised: one CTA per SM
@@ -713,12 +715,13 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   f64tc::k_level0_f64tc<false, f64tc::kSlots><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
       tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,
-      ctx->d_flags);
+      ctx->d_flags, skip);
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
 
-int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride) {
+int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride,
+                        const int* skip) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
   if (mas->n_coarse_jobs == 0) return GS_OK;
   // a few hundred coarse domains at most: a deeper ring per CTA shortens the
@@ -730,7 +733,7 @@ int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, doub
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
   f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(
       tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,
-      f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags);
+      f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags, skip);
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

@@ -290,11 +290,11 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   const int poll = 4;
   int* h_conv = ctx->h_pinned + 64;
   for (int it = 0; it < max_iter; ++it) {
-    GS_TRY(spmv_launch(ctx, mat, p, Ap, nrhs, variant));
+    GS_TRY(spmv_launch_skip(ctx, mat, p, Ap, nrhs, variant, &s->all_conv));
     { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<vg, kRedThreads, 0, st>>>(p, Ap, nullptr, len, nrhs, s, partials, kOpPAp); }
     { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_xr<<<vg, kRedThreads, 0, st>>>(x, r, p, Ap, len, nrhs, s, partials, tol2); }
     if (it + 1 == max_iter) break;
-    GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
+    GS_TRY(mas_apply_launch_skip(ctx, mas, r, z, nrhs, rl, zl, &s->all_conv));
     { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<false><<<vg, kRedThreads, 0, st>>>(r, z, nullptr, len, nrhs, s, partials, kOpRz); }
     { GS_PROF(ctx, GS_K_PCG_VECTOR); k_update_p<<<vg, kRedThreads, 0, st>>>(p, z, len, s); }
     if ((it + 1) % poll == 0) {

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(256) k_spmv_row(const int32_t* __restrict__ ro
                                                   const int32_t* __restrict__ lo_idx,
                                                   const int32_t* __restrict__ lo_col, const double* __restrict__ au,
                                                   int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
-                                                  double* __restrict__ y) {
+                                                  double* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // every RHS of the solve has converged
   spmv_row_group<kLanes, kR>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, row_order, row_ptr, cid, lo_ptr, lo_idx,
                              lo_col, au, n, stride, nrhs, x, y);
 }
@@ -175,7 +176,9 @@ __global__ void __maxnreg__(88) k_spmv_row_ws(const int32_t* __restrict__ row_or
                                               const int32_t* __restrict__ lo_ptr, const int32_t* __restrict__ lo_idx,
                                               const int32_t* __restrict__ lo_col, const double* __restrict__ au,
                                               int32_t n, int64_t stride, int nrhs, const double* __restrict__ x,
-                                              double* __restrict__ y, int* __restrict__ counter) {
+                                              double* __restrict__ y, int* __restrict__ counter,
+                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;  // every RHS of the solve has converged
   const int lane = threadIdx.x & 31;
   const int64_t chunks = ((int64_t)n * kLanes + 31) / 32;
 #pragma unroll 1
@@ -309,6 +312,13 @@ int ensure_row_order(gs_ctx ctx, gs_mat m) {
 
 // y = A x on the context stream (no validation; used inside PCG).
 int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant) {
+  return spmv_launch_skip(ctx, m, x, y, nrhs, variant, nullptr);
+}
+
+// The same, but the row kernels return at once while *skip (device) is set:
+// PCG passes its all-converged word, so the iterations between the last
+// convergence and the host's next poll cost no SpMV work.
+int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant, const int* skip) {
   cudaStream_t st = ctx->stream;
   const int64_t stride = 3LL * m->n;
   if (variant == GS_SPMV_SRBK) {
@@ -328,26 +338,26 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
       const int wgrid = std::min(grid, 2 * ctx->sm_count);  // 88 registers: two blocks of 256 per SM
       GS_PROF(ctx, GS_K_SPMV);
       if (nrhs == 1) {
-        if (lanes == 8) k_spmv_row_ws<8, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else if (lanes == 2) k_spmv_row_ws<2, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else if (lanes == 1) k_spmv_row_ws<1, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else k_spmv_row_ws<4, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        if (lanes == 8) k_spmv_row_ws<8, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else if (lanes == 2) k_spmv_row_ws<2, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else if (lanes == 1) k_spmv_row_ws<1, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else k_spmv_row_ws<4, 1><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
       } else {
-        if (lanes == 8) k_spmv_row_ws<8, 4><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else if (lanes == 2) k_spmv_row_ws<2, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else if (lanes == 1) k_spmv_row_ws<1, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
-        else k_spmv_row_ws<4, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter);
+        if (lanes == 8) k_spmv_row_ws<8, 4><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else if (lanes == 2) k_spmv_row_ws<2, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else if (lanes == 1) k_spmv_row_ws<1, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
+        else k_spmv_row_ws<4, 8><<<wgrid, 256, 0, st>>>(GS_ROW_ARGS, counter, skip);
       }
     } else if (nrhs == 1) {
-      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 1><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
     } else {
-      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 4><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
-      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS); }
+      if (lanes == 8) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<8, 4><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else if (lanes == 2) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<2, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else if (lanes == 1) { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<1, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
+      else { GS_PROF(ctx, GS_K_SPMV); k_spmv_row<4, 8><<<grid, 256, 0, st>>>(GS_ROW_ARGS, skip); }
     }
 #undef GS_ROW_ARGS
   }
