@@ -8,8 +8,13 @@
 // GS_SPMV_ROW gathers each row instead: y_r = sum_{c >= r} A_rc x_c +
 // sum_{c < r} A_cr^T x_c, the second sum reading the same stored blocks
 // through a per-row list of transposed references (4-byte indices, built
-// once per matrix).  Eight lanes share a row and reduce in a fixed order,
-// so results are bit-reproducible and need no atomics or zeroing.
+// once per matrix).  1, 2, 4 or 8 lanes share a row (GS_TUNE_SPMV_LANES) and
+// reduce in a fixed order, so results are bit-reproducible and need no
+// atomics or zeroing.  Rows are taken longest first within windows of
+// consecutive rows (GS_TUNE_SPMV_WINDOW), so the warps see rows of equal
+// length while the rows in flight stay neighbours in the mesh, and by
+// default a persistent grid's warps take the next rows from a counter
+// (GS_TUNE_SPMV_WS).
 //
 // On GB300 both are bound by FP64 FMA throughput (18 FMA per stored block
 // per right-hand side against 80 bytes per block read once for all RHS).
