@@ -50,6 +50,21 @@ def test_binding_constants_match_the_header():
         assert getattr(binding, name) == int(value.strip("()")), name
 
 
+def test_autotuner_knows_every_tuning_parameter():
+    """Every GS_TUNE_* parameter of the header has a name and a candidate list
+    in the autotuner (bench.py copies the tuned values to every stream's
+    context through that list)."""
+    from paper_2411_06224_gb300 import autotune, binding
+
+    params = {getattr(binding, n) for n in dir(binding) if n.startswith("GS_TUNE_") and n != "GS_TUNE_COUNT"}
+    assert params == set(range(binding.GS_TUNE_COUNT))
+    assert set(autotune.CANDIDATES) == params
+    assert set(autotune.NAMES) == params
+    assert len(set(autotune.NAMES.values())) == len(params)
+    for p, values in autotune.CANDIDATES.items():
+        assert len(values) >= 2 and len(set(values)) == len(values), p
+
+
 def test_library_exports_every_declared_symbol(B):
     names = declared()
     L = ctypes.CDLL(B.LIB_PATH)
