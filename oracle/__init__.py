@@ -12,13 +12,17 @@ It restates, in numpy, what the paper's hot path computes:
   reduction (Sec. 5.1).
 * ``partition`` -- the level-0 domain partition with padding (Sec. 3.2,
   Eq. num_subdomains, supplement Algorithm 1).  METIS is replaced by a
-  deterministic greedy graph-growing partitioner, fully specified in that
-  module.
+  deterministic recursive coordinate bisection of the rest positions, fully
+  specified in that module.
 * ``mas``       -- connectivity-enhanced MAS levels (supplement Algorithms 2-5),
   level matrices (Algorithm 1 of the paper), per-domain inverses, and the
   preconditioner apply of supplement Eq. 4-6.
-* ``pcg``       -- preconditioned conjugate gradients (Sec. 3.2).
-* ``spmv``      -- the symmetric block SpMV (Sec. 5.3) by its definition.
+* ``pcg``       -- preconditioned conjugate gradients (Sec. 3.2), and the
+  symmetric block SpMV (Sec. 5.3) by its definition: ``pcg.spmv`` on the
+  stored blocks, ``pcg.SymmetricMatrix`` as a scipy BSR operator.
+* ``adjoint``   -- gradients of a loss through x = H^-1 b.
+* ``strain_limit`` -- the cubic strain-limiting energy of Sec. 4 and its
+  analytic eigensystem (input generation).
 
 Every floating-point quantity is float64.
 """

@@ -153,6 +153,53 @@ def test_symmetric_spmv_equals_dense_product():
     assert np.allclose(A, A.T)
 
 
+def test_symmetric_matrix_operator_worked_example():
+    # Sec. 5.3: a stored off-diagonal block H = A_rc stands for A_rc = H and
+    # A_cr = H^T.  One non-symmetric block between rows 0 and 2 of a 3-row
+    # matrix, worked by hand: y_0 = H x_2, y_2 = H^T x_0, y_1 = D x_1.
+    H = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [7.0, 8.0, 9.0]])
+    D = np.diag([2.0, 3.0, 5.0])
+    x = np.array([1.0, -1.0, 2.0, 0.5, 0.25, -2.0, 3.0, 0.0, -1.0])
+    A = pcg.SymmetricMatrix(3, [0, 1], [2, 1], np.stack([H, D]))
+    y = A(x)
+    want = np.array([1 * 3 + 3 * -1, 4 * 3 + 6 * -1, 7 * 3 + 9 * -1,  # H x_2
+                     2 * 0.5, 3 * 0.25, 5 * -2.0,  # D x_1
+                     1 * 1 + 4 * -1 + 7 * 2, 2 * 1 + 5 * -1 + 8 * 2, 3 * 1 + 6 * -1 + 9 * 2])  # H^T x_0
+    assert np.array_equal(y, want)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_symmetric_matrix_operator_entrywise(seed):
+    # The scipy BSR operator that checks the full-size SpMV and writes the
+    # golden iteration counts, against an entry-by-entry dense matrix built
+    # from the definition (A[3r+a, 3c+b] = H[a, b], A[3c+b, 3r+a] = H[a, b])
+    # and against the loop-based pcg.spmv.  The off-diagonal blocks are not
+    # symmetric, so a missing transpose or a swapped index fails; duplicate
+    # stored keys are absent by construction (assembly output).
+    s = _tiny_system(n=4, contacts=5, seed=seed + 3)
+    rid, cid, au = assembly.assemble(s.rows, s.cols, s.blocks)
+    rng = np.random.default_rng(seed)
+    au = au + np.where((rid != cid)[:, None, None], rng.normal(size=au.shape), 0.0)
+    V = s.n_vertices
+    Ad = np.zeros((3 * V, 3 * V))
+    for r, c, H in zip(rid.tolist(), cid.tolist(), au):
+        for a in range(3):
+            for b in range(3):
+                Ad[3 * r + a, 3 * c + b] += H[a, b]
+                if r != c:
+                    Ad[3 * c + b, 3 * r + a] += H[a, b]
+    Aop = pcg.SymmetricMatrix(V, rid, cid, au)
+    X = rng.normal(size=(3 * V, 3))
+    ref = Ad @ X
+    scale = np.abs(Ad) @ np.abs(X)
+    assert np.all(np.abs(Aop(X) - ref) <= 1e-12 * scale)  # (3n, k) operand
+    for k in range(3):
+        assert np.all(np.abs(Aop(X[:, k]) - ref[:, k]) <= 1e-12 * scale[:, k])
+        y = pcg.spmv(rid, cid, au, X[:, k].reshape(V, 3)).ravel()
+        assert np.all(np.abs(y - ref[:, k]) <= 1e-12 * scale[:, k])
+    assert np.array_equal(Aop.A.toarray() != 0, Ad != 0)
+
+
 # ---------------------------------------------------------------- partition (Sec. 3.2)
 
 
