@@ -116,6 +116,15 @@ int gs_mat_destroy(gs_mat mat);
 #define GS_SPMV_SRBK 0 /* Alg. SRBK: upper blocks, warp segmented reduce + transposed atomics */
 #define GS_SPMV_ROW 1  /* row-gather over the upper blocks and their transposes; no atomics,
                           bit-reproducible */
+#define GS_SPMV_ROW_FF 2 /* the row-gather product in float-float arithmetic on the FP32 units:
+                            A (scaled by powers of two per block row, once per matrix) and x
+                            (scaled per RHS) split into pairs of floats, products and sums by
+                            error-free transformations (exact product by FMA, Knuth's
+                            two-sum).  Error per entry at most ((3m+1)(m+3) + 4) u^2 (|A||x|)_i,
+                            u = 2^-24, m = 3 x the row's stored blocks of both triangles
+                            (1.8e-11 for a 13-block row; FP64 sums are within m 2^-53);
+                            terms below 2^-100 of the row's largest lose their low part.
+                            Bit-reproducible; same launch shapes as GS_SPMV_ROW */
 
 /* y = A x for nrhs right-hand sides (Sec. 5.3), A the full symmetric matrix
  * whose diagonal and upper blocks `mat` stores.  x, y: device
@@ -353,6 +362,20 @@ int gs_profile_begin(gs_ctx ctx, uint32_t timed_classes);
  * int64[GS_K_COUNT]) and summed event time in ms (host double[GS_K_COUNT],
  * 0 for untimed classes).  Either output may be NULL. */
 int gs_profile_end(gs_ctx ctx, int64_t* launches, double* ms);
+
+/* Device allocations the library has made on `ctx` so far (stream-ordered
+ * pool allocations of matrices, preconditioners and scratch; gs_create's own
+ * 256-byte flag word is not counted): their number and total bytes.  Either
+ * output may be NULL.  Lets a caller check that a call allocated nothing. */
+int gs_ctx_alloc_stats(gs_ctx ctx, int64_t* n_allocs, int64_t* bytes);
+
+/* Testing aid: OR `flags` into the context's device error word, as a kernel
+ * whose check failed would (bits: 1 index out of range, 2 not positive
+ * definite, 4 non-finite, 8 a bounded wait gave up).  The next call that
+ * reads the word reports the matching status and clears it.  It stands in
+ * for a device-side failure without making one.  GS_ERR_INVALID for unknown
+ * bits. */
+int gs_debug_raise_flags(gs_ctx ctx, int32_t flags);
 
 #ifdef __cplusplus
 }

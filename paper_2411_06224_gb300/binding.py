@@ -86,6 +86,8 @@ EXPORTS = [
     "gs_tune_get",
     "gs_micro_segment_reduce",
     "gs_micro_bsr_spmv_cusparse",
+    "gs_ctx_alloc_stats",
+    "gs_debug_raise_flags",
 ]
 
 
@@ -155,6 +157,8 @@ def lib():
                                                            ctypes.POINTER(ctypes.c_float)]),
             "gs_tune_get": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32)]),
             "gs_profile_end": (ctypes.c_int, [_P, _P, _P]),
+            "gs_ctx_alloc_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+            "gs_debug_raise_flags": (ctypes.c_int, [_P, _I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -428,6 +432,17 @@ def gs_tune_get(ctx, param):
     v = _I32()
     _check(lib().gs_tune_get(ctx, param, ctypes.byref(v)), "gs_tune_get")
     return v.value
+
+
+def gs_ctx_alloc_stats(ctx):
+    """(number, total bytes) of the device allocations the library made on ctx."""
+    n, b = _I64(), _I64()
+    _check(lib().gs_ctx_alloc_stats(ctx, ctypes.byref(n), ctypes.byref(b)), "gs_ctx_alloc_stats")
+    return n.value, b.value
+
+
+def gs_debug_raise_flags(ctx, flags):
+    _check(lib().gs_debug_raise_flags(ctx, flags), "gs_debug_raise_flags")
 
 
 # ----------------------------------------------------------------- microbenchmarks

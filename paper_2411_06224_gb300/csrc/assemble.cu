@@ -238,6 +238,8 @@ int gs_mat_destroy(gs_mat m) {
   c->release(m->lo_idx);
   c->release(m->lo_col);
   c->release(m->au32);
+  c->release(m->au_ff);
+  c->release(m->ff_k);
   c->release(m->row_order);
   c->release(m->key_of_input);
   delete m;

@@ -89,6 +89,8 @@ struct gs_ctx_s {
   int* d_flags = nullptr;     // 256 device bytes: [0] error word, [kSpmvCounterWord] SpMV work counter
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
   std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls
+  int64_t n_allocs = 0;       // device allocations made through alloc() so far
+  int64_t alloc_bytes = 0;    // and their total size
 
   // Stream-ordered allocation on this context's stream.
   int alloc(void** p, size_t bytes);
@@ -118,6 +120,7 @@ enum ScratchSlot : int {
   kSlotMasBuild1,
   kSlotMasBuild2,
   kSlotMasBuild3,
+  kSlotFFSplit,
   kSlotCount
 };
 
@@ -162,6 +165,13 @@ int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, doub
 int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant, const int* skip);
 int mas_apply_launch_skip(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl,
                           const int* skip);
+// Float-float SpMV (spmv_ff.cu).  ensure_ff builds the matrix's scaled
+// float-float copy once.  spmv_ff_split_launch: y = A x from x already split
+// as xs[k * 3n + i] = (hi, lo) of x * 2^(ff_k[node] - F[k]) (|.| <= 1), F
+// device int[nrhs]; spmv_ff_launch splits x itself (two extra passes).
+int ensure_ff(gs_ctx ctx, gs_mat m);
+int spmv_ff_split_launch(gs_ctx ctx, gs_mat m, const float2* xs, const int* F, double* y, int nrhs, const int* skip);
+int spmv_ff_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, const int* skip);
 }  // namespace gs
 
 struct gs_mat_s {
@@ -181,6 +191,12 @@ struct gs_mat_s {
   int32_t* key_of_input = nullptr;  // per input block: index of the stored block it was summed into, -1 if dropped
   int64_t n_input = 0;
   float* au32 = nullptr;      // FP32 copy of au for the mixed-precision solve (built lazily)
+  // Float-float copy for GS_SPMV_ROW_FF (built lazily): block (r, c) scaled by
+  // 2^-(k_r + k_c), k_i = ceil(E_i / 2) with 2^E_i bounding row i's largest
+  // entry, so every scaled entry is below 1 in magnitude; stored per entry as
+  // (hi, lo) = (rn(a), rn(a - hi)) floats.
+  float2* au_ff = nullptr;    // nnzb * 9
+  int32_t* ff_k = nullptr;    // n + 1: k_i - K per row; [n] holds K = max_i k_i
   gs_ctx owner = nullptr;
 };
 
@@ -192,6 +208,8 @@ struct gs_mas_s {
   std::vector<int32_t> n_items;    // per level (level 0: padded slots)
   std::vector<int32_t> n_domains;  // per level
   std::vector<int32_t*> coarse;    // per level: device int32[n] (level 0 = map)
+  std::vector<int32_t*> up;        // per level l >= 1 below the top: device int32[n_domains[l] * N],
+                                   // the level-(l+1) item of each level-l item (-1: padding)
   int32_t* remap0 = nullptr;       // device int32[n_items[0]], slot -> node or -1
   std::vector<double*> inv64;      // per level: n_domains * (3N)^2
   std::vector<float*> inv32;       // per level (FP32 precision, or made for the mixed solve)

@@ -69,6 +69,8 @@ int gs_ctx_s::alloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return GS_OK;
   GS_CUDA(cudaMallocAsync(p, bytes, stream));
+  n_allocs += 1;
+  alloc_bytes += (int64_t)bytes;
   return GS_OK;
 }
 
@@ -211,6 +213,24 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value) {
   GS_CHECK(ctx && value && param >= 0 && param < GS_TUNE_COUNT, GS_ERR_INVALID, "gs_tune_get: bad argument");
   *value = ctx->tune[param];
+  return GS_OK;
+}
+
+int gs_ctx_alloc_stats(gs_ctx ctx, int64_t* n_allocs, int64_t* bytes) {
+  GS_CHECK(ctx, GS_ERR_INVALID, "gs_ctx_alloc_stats: null context");
+  if (n_allocs) *n_allocs = ctx->n_allocs;
+  if (bytes) *bytes = ctx->alloc_bytes;
+  return GS_OK;
+}
+
+int gs_debug_raise_flags(gs_ctx ctx, int32_t flags) {
+  GS_CHECK(ctx, GS_ERR_INVALID, "gs_debug_raise_flags: null context");
+  GS_CHECK((flags & ~15) == 0, GS_ERR_INVALID, "gs_debug_raise_flags: unknown bits 0x%x", flags);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  GS_CUDA(cudaStreamSynchronize(ctx->stream));
+  GS_CUDA(cudaMemcpy(ctx->h_pinned, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  ctx->h_pinned[0] |= flags;
+  GS_CUDA(cudaMemcpy(ctx->d_flags, ctx->h_pinned, sizeof(int), cudaMemcpyHostToDevice));
   return GS_OK;
 }
 

@@ -3,8 +3,9 @@
 // The coarseners map level 0 directly to every level, so all levels are
 // independent once the restricted vectors exist:
 //   1. k_restrict: one warp per level-0 domain gathers its nodes' residuals
-//      and sums them per coarse item (usually one item per domain: one warp
-//      reduction and one atomic per component), for every level >= 1;
+//      and sums them per level-1 item (an item lies inside one domain, so
+//      the warp stores its sums); k_restrict_up then sums each level's items
+//      into the next level's, one warp per domain, in a fixed order;
 //   2. k_domain_product on the coarse levels: z_l = M_l^{-1} r_l per domain;
 //   3. k_domain_product on level 0 fused with the prolongation: each node's
 //      z = (M_0^{-1} r)_slot + sum_l z_l[coarse_l(node)], written once.
@@ -84,12 +85,8 @@ __global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(const double* 
         }
       }
       left &= ~g;
-      const int32_t lead_node = __shfl_sync(kFull, node, lead);
-      if (act) {
-        const int64_t o = k * lstride + c;
-        atomicAdd(&rl[o + 3 * (al.vec_off[1] + cc)], sum);
-        for (int l = 2; l < al.L; ++l) atomicAdd(&rl[o + 3 * (al.vec_off[l] + al.coarse[l][lead_node])], sum);
-      }
+      // a level-1 item lies inside this domain: this warp is its only writer
+      if (act) rl[k * lstride + c + 3 * (al.vec_off[1] + cc)] = sum;
     }
   }
 }
@@ -208,6 +205,12 @@ static int launch_apply(gs_ctx ctx, gs_mas mas, const Ts* const* d_inv, const in
     GS_CUDA(cudaMemsetAsync(rl, 0, (size_t)nrhs * lstride * sizeof(double), st));
     { GS_PROF(ctx, GS_K_MAS_APPLY_COARSE); k_restrict<<<ceil_div(mas->n_domains[0], kRestrictWarps), 32 * kRestrictWarps, 0, st>>>(r, stride, nrhs, mas->remap0,
                                                                               mas->n_domains[0], al, rl, lstride, skip); }
+    for (int l = 1; l + 1 < mas->L; ++l) {  // levels >= 2 from the level below, in a fixed order
+      GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
+      k_restrict_up<double, LevelIdxRhsMajor><<<ceil_div((int64_t)mas->n_domains[l] * 32, 128), 128, 0, st>>>(
+          mas->up[l], mas->n_domains[l], N, 3 * nrhs, LevelIdxRhsMajor{lstride, mas->vec_off[l]},
+          LevelIdxRhsMajor{lstride, mas->vec_off[l + 1]}, rl, skip);
+    }
     if (level0_f64tc_usable(ctx, mas, nrhs)) {  // FP64 accuracy on the BF16 tensor cores
       GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
       GS_TRY(coarse_f64tc_launch(ctx, mas, nrhs, rl, zl, lstride, skip));

@@ -15,9 +15,13 @@
 // address, so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; that first
 // call per device should therefore be made before any stream capture
-// begins.  All calls share the array: the restricted vectors are cleared at
-// the start of every call, and two calls whose work overlaps on the GPU
-// (different streams, or different threads on one device) race on it.
+// begins.  The cached address belongs to the device's primary context, so no
+// call may follow a cudaDeviceReset in the same process.  All calls share the
+// array: the restricted vectors are cleared at the start of every call, and
+// two calls whose work overlaps on the GPU (different streams, or different
+// threads on one device) race on it.  Where the level-0 product runs on the
+// tensor cores, the call waits for its stream and returns the status of that
+// product's bounded waits, like gs_mas_apply.
 // With the profiler switched on (gs_profile_begin) the library may create
 // CUDA events; it is off unless the caller turns it on.
 #include <mutex>
@@ -76,5 +80,15 @@ extern "C" int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, dou
   GS_CUDA(cudaSetDevice(ctx->device));
   double* base = nullptr;
   GS_TRY(gs::scratch_address(ctx->device, &base));
-  return gs::mas_apply_launch(ctx, mas, r, z, nrhs, base, base + per);
+  GS_TRY(gs::mas_apply_launch(ctx, mas, r, z, nrhs, base, base + per));
+  if (gs::level0_bf16_on_tensor_cores(ctx, mas, nrhs) || gs::level0_f64tc_usable(ctx, mas, nrhs)) {
+    // The tensor-core kernels end a wait that runs past its limit with a bit
+    // in the context's device error word.  Read and clear it here (a copy
+    // into the context's pinned word, no allocation), so that this call
+    // reports its own timeout and no later call inherits it.
+    int flags = 0;
+    GS_TRY(ctx->take_flags(&flags));
+    if (flags) return gs::status_from_flags(flags);
+  }
+  return GS_OK;
 }

@@ -133,6 +133,16 @@ __global__ void k_next_of_node(const int32_t* __restrict__ item_of_node, int32_t
   next_of_node[u] = dom_off[a / N] + local_id[a];
 }
 
+// Parent (level-(l+1) item) of every level-l item, l >= 1, from the same
+// numbering as k_next_of_node; -1 for padded (empty) items.
+__global__ void k_up_of_item(int32_t n_items_pad, int N, const int32_t* __restrict__ local_id,
+                             const int32_t* __restrict__ dom_off, int32_t* __restrict__ up) {
+  int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_items_pad) return;
+  const int32_t id = local_id[a];
+  up[a] = id >= 0 ? dom_off[a / N] + id : -1;
+}
+
 // ------------------------------------------------------------------ level matrices
 struct LevelPtrs {
   const int32_t* coarse[8];
@@ -404,6 +414,7 @@ int gs_mas_destroy(gs_mas mas) {
   if (!mas) return GS_OK;
   gs_ctx c = mas->owner;
   for (auto p : mas->coarse) c->release(p);
+  for (auto p : mas->up) c->release(p);
   for (auto p : mas->inv64) c->release(p);
   for (auto p : mas->inv32) c->release(p);
   for (auto p : mas->inv16) c->release(p);
@@ -516,12 +527,20 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     if ((s = ctx->alloc((void**)&cn, (size_t)n * 4))) return fail(s);
     mas->coarse.push_back(cn);
     { GS_PROF(ctx, GS_K_MAS_LEVELS); k_next_of_node<<<ceil_div(n, 256), 256, 0, st>>>(cl, n, N, local_id, dom_off, cn); }
+    mas->up.resize(l + 1, nullptr);
+    if (l >= 1) {  // item-to-item map for the ordered restriction of level l + 1
+      int32_t* u = nullptr;
+      if ((s = ctx->alloc((void**)&u, (size_t)ndom * N * 4))) return fail(s);
+      mas->up[l] = u;
+      { GS_PROF(ctx, GS_K_MAS_LEVELS); k_up_of_item<<<ceil_div((int64_t)ndom * N, 256), 256, 0, st>>>(ndom * N, N, local_id, dom_off, u); }
+    }
     mas->n_items.push_back(n_next);
     mas->n_domains.push_back(ceil_div(n_next, N));
     n_real = n_next;
   }
   mas->L = (int)mas->coarse.size();
   const int L = mas->L;
+  mas->up.resize(L, nullptr);
   // level matrices
   const int ld = 3 * N;
   LevelPtrs lp{};

@@ -386,20 +386,20 @@ __global__ void k_restrict32(const float* __restrict__ r, const int32_t* __restr
   float v[3 * R];
 #pragma unroll
   for (int q = 0; q < 3 * R; ++q) v[q] = real ? r[(int64_t)node * R * 3 + q] : 0.0f;
-  for (int l = 1; l < al.L; ++l) {
-    const int32_t c = real ? al.coarse[l][node] : -1;
-    uint32_t left = __ballot_sync(kFull, real);
-    while (left) {
-      const int lead = __ffs(left) - 1;
-      const int32_t cc = __shfl_sync(kFull, c, lead);
-      const uint32_t g = __ballot_sync(kFull, real && c == cc);
-      left &= ~g;
-      const bool mine = (g >> lane) & 1u;
+  // level 1 only: its items lie inside this domain, so the warp stores each
+  // item's sum; coarser levels follow from level 1 in k_restrict_up
+  const int32_t c = real ? al.coarse[1][node] : -1;
+  uint32_t left = __ballot_sync(kFull, real);
+  while (left) {
+    const int lead = __ffs(left) - 1;
+    const int32_t cc = __shfl_sync(kFull, c, lead);
+    const uint32_t g = __ballot_sync(kFull, real && c == cc);
+    left &= ~g;
+    const bool mine = (g >> lane) & 1u;
 #pragma unroll
-      for (int q = 0; q < 3 * R; ++q) {
-        float t = warp_sum(mine ? v[q] : 0.0f);
-        if (lane == 0) atomicAdd(&rl[(al.vec_off[l] + cc) * R * 3 + q], t);
-      }
+    for (int q = 0; q < 3 * R; ++q) {
+      float t = warp_sum(mine ? v[q] : 0.0f);
+      if (lane == 0) rl[(al.vec_off[1] + cc) * R * 3 + q] = t;
     }
   }
 }
@@ -564,6 +564,12 @@ static int solve_mixed(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b, int 
         GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
         k_restrict32<R><<<ceil_div((int64_t)mas->n_domains[0] * 32, 256), 256, 0, st>>>(rr, mas->remap0,
                                                                                        mas->n_domains[0], al, rl, s);
+      }
+      for (int l = 1; l + 1 < mas->L; ++l) {  // levels >= 2 from the level below, in a fixed order
+        GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);
+        k_restrict_up<float, LevelIdxNodeMajor><<<ceil_div((int64_t)mas->n_domains[l] * 32, 128), 128, 0, st>>>(
+            mas->up[l], mas->n_domains[l], N, 3 * R, LevelIdxNodeMajor{mas->vec_off[l], 3 * R},
+            LevelIdxNodeMajor{mas->vec_off[l + 1], 3 * R}, rl, &s->all_out);
       }
       {
         GS_PROF(ctx, GS_K_MAS_APPLY_COARSE);

@@ -46,4 +46,49 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Addresses of the multilevel restricted vectors: value v = 3 k + c (RHS k,
+// component c) of item `item` of one level.  RHS-major (FP64 apply):
+// rl[k * lstride + 3 (off + item) + c]; node-major (FP32 inner solve):
+// rl[(off + item) * nv + v].
+struct LevelIdxRhsMajor {
+  int64_t lstride, off;
+  __device__ __forceinline__ int64_t operator()(int64_t item, int v) const {
+    return (int64_t)(v / 3) * lstride + 3 * (off + item) + v % 3;
+  }
+};
+struct LevelIdxNodeMajor {
+  int64_t off;
+  int nv;
+  __device__ __forceinline__ int64_t operator()(int64_t item, int v) const { return (off + item) * nv + v; }
+};
+
+// Restriction from level l >= 1 to level l + 1 (supplement Eq. 5-6, C_{l+1}
+// = C'_l C_l).  A level-(l+1) item is a connected component of one level-l
+// domain (items dN .. dN+N-1), so one warp per level-l domain sums the
+// values of each parent's items in ascending lane order and stores the total:
+// every parent has one writer and a fixed order of addition, so the result
+// does not depend on scheduling.  up[a]: the parent of item a (-1: none).
+// Lanes own values v = lane, lane + 32, ... < nv.
+template <typename T, typename Idx>
+__global__ void __launch_bounds__(128) k_restrict_up(const int32_t* __restrict__ up, int32_t n_dom, int N, int nv,
+                                                     Idx src, Idx dst, T* __restrict__ rl,
+                                                     const int* __restrict__ skip) {
+  if (skip && *skip) return;  // every RHS of the solve has converged
+  const int32_t d = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (d >= n_dom) return;  // whole warp
+  const int32_t par = lane < N ? up[(int64_t)d * N + lane] : -1;
+  uint32_t left = __ballot_sync(kFull, par >= 0);
+  while (left) {
+    const int32_t pp = __shfl_sync(kFull, par, __ffs(left) - 1);
+    const uint32_t g = __ballot_sync(kFull, par == pp);
+    left &= ~g;
+    for (int v = lane; v < nv; v += 32) {
+      T sum = (T)0;
+      for (uint32_t m = g; m; m &= m - 1) sum += rl[src((int64_t)d * N + (__ffs(m) - 1), v)];
+      rl[dst(pp, v)] = sum;
+    }
+  }
+}
+
 }  // namespace gs

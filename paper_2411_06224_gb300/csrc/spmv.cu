@@ -326,6 +326,7 @@ int spmv_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int 
 int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant, const int* skip) {
   cudaStream_t st = ctx->stream;
   const int64_t stride = 3LL * m->n;
+  if (variant == GS_SPMV_ROW_FF) return spmv_ff_launch(ctx, m, x, y, nrhs, skip);
   if (variant == GS_SPMV_SRBK) {
     GS_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * stride * sizeof(double), st));
     if (m->nnzb > 0)
@@ -376,7 +377,8 @@ extern "C" int gs_spmv(gs_ctx ctx, gs_mat m, const double* x, double* y, int32_t
   GS_CHECK(ctx && m, GS_ERR_INVALID, "gs_spmv: null context or matrix");
   GS_CHECK(nrhs >= 1, GS_ERR_INVALID, "gs_spmv: nrhs %d", nrhs);
   GS_CHECK(x && y && x != y, GS_ERR_INVALID, "gs_spmv: null or aliased vectors");
-  GS_CHECK(variant == GS_SPMV_SRBK || variant == GS_SPMV_ROW, GS_ERR_INVALID, "gs_spmv: variant %d", variant);
+  GS_CHECK(variant == GS_SPMV_SRBK || variant == GS_SPMV_ROW || variant == GS_SPMV_ROW_FF, GS_ERR_INVALID,
+           "gs_spmv: variant %d", variant);
   GS_CUDA(cudaSetDevice(ctx->device));
   return gs::spmv_launch(ctx, m, x, y, nrhs, variant);
 }

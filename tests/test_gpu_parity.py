@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+import fp64bounds
 from oracle import assembly, mas, partition, pcg
 from synth.workloads import make_tet_system, plain_small, rhs
 
@@ -218,15 +219,10 @@ def test_mas_apply_matches_oracle(B, ctx, name, N, L, nrhs):
     z = torch.empty((nrhs, 3 * V), dtype=torch.float64, device="cuda")
     B.gs_mas_apply(ctx, bt.mas, dev(r, torch.float64), z, nrhs=nrhs)
     z0 = bt.omas(r)
-    lv = bt.omas.levels
-    kappa = max(
-        _domain_cond(bt.omas.mats[l][d], (np.arange(d * N, d * N + N) < lv.n_items[l])
-                     & np.pad(lv.real[l], (0, lv.n_domains(l) * N - lv.n_items[l]))[d * N : d * N + N])
-        for l in range(lv.n_levels) for d in range(lv.n_domains(l))
-    )
-    for k in range(nrhs):
-        err = np.linalg.norm(z.cpu().numpy()[k] - z0[k]) / np.linalg.norm(z0[k])
-        assert err <= EPS_SUM * kappa * 10, (err, kappa)
+    # entry by entry: sum reordering plus each domain's inverse error
+    bound = fp64bounds.apply_bound(bt.omas, r)
+    dz = np.abs(z.cpu().numpy() - z0)
+    assert np.all(dz <= bound), (dz / bound).max()
     bt.close()
 
 
@@ -255,9 +251,12 @@ def test_pcg_fixed_iterations_follow_oracle_recurrence(B, ctx, name, N, L, k):
     assert st == B.GS_ERR_MAXITER and list(it) == [k] * nrhs
     mv = lambda v: pcg.spmv(bt.rid, bt.cid, bt.au, v.reshape(-1, 3)).ravel()
     x0, _, _ = pcg.pcg(mv, lambda v: bt.omas(v), b, fixed_iters=k)
+    # entry by entry along the same recurrence: rounding differences, relative
+    # to the entry with a floor at the RHS's root-mean-square entry
+    xg = x.cpu().numpy()
     for q in range(nrhs):
-        err = np.linalg.norm(x.cpu().numpy()[q] - x0[q]) / np.linalg.norm(x0[q])
-        assert err <= 1e-9, err
+        rms = np.sqrt(np.mean(x0[q] ** 2))
+        assert np.all(np.abs(xg[q] - x0[q]) <= 1e-9 * (np.abs(x0[q]) + rms)), q
     bt.close()
 
 
