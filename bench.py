@@ -60,8 +60,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--grid", type=int, default=64, help="vertices per cube edge (64 = the named workload)")
     p.add_argument("--nrhs", type=int, default=8)
+    p.add_argument("--sweep", default="1e5,1e7,1e9",
+                   help="Young's moduli of the step's systems (the named workload: 1e5,1e7,1e9; a single value "
+                        "keeps profiling runs small)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    p.add_argument("--spmv", default="row", choices=["row", "srbk"])
+    p.add_argument("--spmv", default="row", choices=["row", "srbk", "ff"],
+                   help="row: FP64 row gather; srbk: the paper's SRBK; ff: row gather in float-float on the FP32 units")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
     p.add_argument("--no-lanes", dest="lanes", action="store_false",
@@ -184,12 +188,12 @@ def autotune_current(B, ctx):
     return autotune.current(ctx)
 
 
-def make_workload(grid, nrhs, rank):
+def make_workload(grid, nrhs, rank, Es=(1e5, 1e7, 1e9)):
     import numpy as np
 
     from synth.workloads import rhs, stiffness_sweep
 
-    systems = stiffness_sweep(n=grid, seed=1002 + rank)
+    systems = stiffness_sweep(Es=tuple(Es), n=grid, seed=1002 + rank)
     b = rhs(3 * systems[0].n_vertices, nrhs, seed0=2000 + 100 * rank)
     return systems, np.ascontiguousarray(b)
 
@@ -220,11 +224,11 @@ def main():
     from paper_2411_06224_gb300 import binding as B
 
     dev = torch.device("cuda", local)
-    systems, b_host = make_workload(args.grid, args.nrhs, rank)
+    systems, b_host = make_workload(args.grid, args.nrhs, rank, Es=[float(e) for e in args.sweep.split(",")])
     V = systems[0].n_vertices
     N, L = 32, 3
     prec = B.GS_PREC_FP32 if args.precision == "fp32" else B.GS_PREC_FP64
-    variant = B.GS_SPMV_ROW if args.spmv == "row" else B.GS_SPMV_SRBK
+    variant = {"row": B.GS_SPMV_ROW, "srbk": B.GS_SPMV_SRBK, "ff": B.GS_SPMV_ROW_FF}[args.spmv]
     mp, ndom = B.gs_partition(systems[0].X, N)  # once per mesh, before timing
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     shared = dict(map=t(mp, torch.int32), adj_ptr=t(systems[0].adj_ptr, torch.int32), adj=t(systems[0].adj, torch.int32),
@@ -348,7 +352,8 @@ def main():
         mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
                              domain_size=N, max_levels=L, precision=prec)
         res = autotune.tune(ctx, mat, mas, nrhs=args.nrhs, reps=5, mixed=args.mixed_steps > 0,
-                            fp64=prec == B.GS_PREC_FP64)
+                            fp64=prec == B.GS_PREC_FP64,
+                            spmv_variant=variant if variant != B.GS_SPMV_SRBK else B.GS_SPMV_ROW)
         B.gs_mas_destroy(mas)
         if args.mixed_steps > 0 and args.nrhs <= 8:  # BF16 level-0 product: tensor cores or FP32 cores
             mas = B.gs_build_mas(ctx, mat, shared["map"], ndom, shared["adj_ptr"], shared["adj"], shared["contacts"],
@@ -717,16 +722,35 @@ def main():
         apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
         apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
                                 "(level-0 MAS apply + prolongation)")
-    spmv_ws = args.spmv == "row" and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WS) == 1
-    spmv_traffic = (SPMV_WS_DRAM_BYTES_64.get(B.gs_tune_get(ctx, B.GS_TUNE_SPMV_LANES))
-                    if spmv_ws and args.grid == 64 and args.nrhs == 8
-                    and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WINDOW) == 1024 else None)  # the captured shapes
-    spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, spmv_traffic)
-    spmv_line["kernel"] = "k_spmv_row_ws" if spmv_ws else f"k_spmv_{args.spmv}"
-    # alone: the same arithmetic over the sequential step's durations
-    spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
-                             "achieved": spmv_flops / t_spmv_iso / 1e12,
-                             "frac": spmv_flops / t_spmv_iso / 1e12 / fp64_peak_tflops}
+    spmv_ws = args.spmv in ("row", "ff") and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WS) == 1
+    if args.spmv == "ff":
+        # float-float on the FP32 units: 12 FP32 instructions per term (exact
+        # product, two-sum, small parts), 9 terms per block use and RHS, one use
+        # per diagonal block and two per off-diagonal block
+        ff_inst = args.nrhs * 9 * 12.0 * (V + 2.0 * n_off)
+        fp32_peak = sms * 128 * sm_mhz_max * 1e6 / 1e12  # T FP32 instructions/s
+        spmv_line = {"bound": "alu", "achieved": ff_inst / t_spmv / 1e12, "peak": fp32_peak,
+                     "unit": "T FP32 instructions/s", "frac": ff_inst / t_spmv / 1e12 / fp32_peak, "traffic": None,
+                     "hbm_gbs": spmv_bytes / t_spmv / 1e9, "hbm_frac": spmv_bytes / t_spmv / 1e9 / hbm,
+                     "fp64_equivalent_tflops": spmv_flops / t_spmv / 1e12,
+                     "fp64_equivalent_frac_of_fp64_peak": spmv_flops / t_spmv / 1e12 / fp64_peak_tflops,
+                     "instructions_per_launch": ff_inst, "flops_per_launch": spmv_flops,
+                     "bytes_per_launch": spmv_bytes, "avg_launch_ms": t_spmv * 1e3}
+        spmv_line["kernel"] = "k_spmv_ff_ws" if spmv_ws else "k_spmv_ff_row"
+        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
+                                 "achieved": ff_inst / t_spmv_iso / 1e12,
+                                 "frac": ff_inst / t_spmv_iso / 1e12 / fp32_peak,
+                                 "hbm_frac": spmv_bytes / t_spmv_iso / 1e9 / hbm}
+    else:
+        spmv_traffic = (SPMV_WS_DRAM_BYTES_64.get(B.gs_tune_get(ctx, B.GS_TUNE_SPMV_LANES))
+                        if spmv_ws and args.grid == 64 and args.nrhs == 8
+                        and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WINDOW) == 1024 else None)  # the captured shapes
+        spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, spmv_traffic)
+        spmv_line["kernel"] = "k_spmv_row_ws" if spmv_ws else f"k_spmv_{args.spmv}"
+        # alone: the same arithmetic over the sequential step's durations
+        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
+                                 "achieved": spmv_flops / t_spmv_iso / 1e12,
+                                 "frac": spmv_flops / t_spmv_iso / 1e12 / fp64_peak_tflops}
     apply_iso_ach = (tc_bytes / t_apply_iso / 1e9) if f64tc else (apply_flops / t_apply_iso / 1e12)
     apply_line["isolated"] = {"avg_launch_ms": t_apply_iso * 1e3, "achieved": apply_iso_ach,
                               "frac": apply_iso_ach / apply_line["peak"]}

@@ -120,9 +120,9 @@ int gs_mat_destroy(gs_mat mat);
                             A (scaled by powers of two per block row, once per matrix) and x
                             (scaled per RHS) split into pairs of floats, products and sums by
                             error-free transformations (exact product by FMA, Knuth's
-                            two-sum).  Error per entry at most ((3m+1)(m+3) + 4) u^2 (|A||x|)_i,
+                            two-sum).  Error per entry at most ((3m+1)(m+4) + 6) u^2 (|A||x|)_i,
                             u = 2^-24, m = 3 x the row's stored blocks of both triangles
-                            (1.8e-11 for a 13-block row; FP64 sums are within m 2^-53);
+                            (1.9e-11 for a 13-block row; FP64 sums are within m 2^-53);
                             terms below 2^-100 of the row's largest lose their low part.
                             Bit-reproducible; same launch shapes as GS_SPMV_ROW */
 
@@ -311,7 +311,11 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 #define GS_TUNE_SPMV_WS 7         /* FP64 row SpMV: 1 (default) a persistent grid (two blocks per SM) whose
                                      warps take the next rows of the order from a counter; 0 one thread
                                      group per row */
-#define GS_TUNE_COUNT 8           /* number of parameters */
+#define GS_TUNE_SPMV_FF_RHS 8     /* float-float SpMV (GS_SPMV_ROW_FF): right-hand sides per thread and pass,
+                                     8 (default; the GS_TUNE_SPMV_LANES lanes of a row share its blocks), or
+                                     4 / 2 (each of nrhs / value lanes walks all the row's blocks for its own
+                                     right-hand sides; fewer registers, more resident warps) */
+#define GS_TUNE_COUNT 9           /* number of parameters */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);
 int gs_tune_get(gs_ctx ctx, int32_t param, int32_t* value);
 

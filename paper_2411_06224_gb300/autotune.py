@@ -10,7 +10,7 @@ sums; a shape the problem cannot launch (too many threads per block) is
 skipped.
 
 The shapes and the kernels they steer:
-  * GS_TUNE_SPMV_LANES   lanes per block row of the FP64 row SpMV (Sec. 5.2);
+  * GS_TUNE_SPMV_LANES   lanes per block row of the row SpMV, FP64 or float-float (Sec. 5.3);
   * GS_TUNE_APPLY_RHS    right-hand sides per thread in the level-0 MAS product (Eq. 6);
   * GS_TUNE_SPMV32_LANES lanes per block row of the FP32 SpMV inside the mixed solve;
   * GS_TUNE_BATCH_CHUNK  vector entries per work item of the batched PCG reductions;
@@ -20,6 +20,10 @@ The shapes and the kernels they steer:
                          per SM) or on the FP64 cores;
   * GS_TUNE_SPMV_WS      one thread group per row, or a persistent grid whose
                          warps steal the next rows;
+  * GS_TUNE_SPMV_FF_RHS  right-hand sides per thread of the float-float SpMV
+                         (8: a row's lanes share its blocks; 4 or 2: the lanes
+                         split the right-hand sides, fewer registers and more
+                         resident warps);
   * GS_TUNE_SPMV_WINDOW  rows per window of the SpMV's length order.  Not swept:
                          timed alone the SpMV prefers one global order (the
                          longest rows first also balance its tail), but windows
@@ -41,6 +45,7 @@ CANDIDATES = {
     B.GS_TUNE_F64_TC: (1, 2, 0),
     B.GS_TUNE_SPMV_WINDOW: (0, 256, 1024, 4096, 16384),
     B.GS_TUNE_SPMV_WS: (0, 1),
+    B.GS_TUNE_SPMV_FF_RHS: (8, 4, 2),
 }
 
 NAMES = {
@@ -52,6 +57,7 @@ NAMES = {
     B.GS_TUNE_F64_TC: "fp64_on_tensor_cores",
     B.GS_TUNE_SPMV_WINDOW: "spmv_row_window",
     B.GS_TUNE_SPMV_WS: "spmv_work_stealing",
+    B.GS_TUNE_SPMV_FF_RHS: "spmv_ff_rhs_per_pass",
 }
 
 
@@ -85,7 +91,8 @@ def sweep(ctx, param, klass, fn, reps=10, candidates=None):
     return best, times
 
 
-def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, seed=0, bf16=False, fp64=False):
+def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, seed=0, bf16=False, fp64=False,
+         spmv_variant=B.GS_SPMV_ROW):
     """Tune the shapes a solve on (mat, mas) with `nrhs` right-hand sides uses.
 
     mixed:    also tune the FP32 SpMV of gs_pcg_solve_mixed;
@@ -94,7 +101,10 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     fp64:     `mas` is FP64: also choose the digit-split tensor-core product or
               the FP64-core product for level 0;
     node_off: block-row offsets of a batch (gs_pcg_solve_batch); tunes the
-              reduction chunk on `iters` fixed iterations.
+              reduction chunk on `iters` fixed iterations;
+    spmv_variant: the SpMV whose shapes are tuned (GS_SPMV_ROW or the
+              float-float GS_SPMV_ROW_FF; they share the lane and schedule
+              parameters).
     Returns {name: (best value, {value: ms per launch})}.
     """
     n = B.gs_mat_info(mat)[0]
@@ -102,10 +112,12 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     x = torch.randn((nrhs, 3 * n), dtype=torch.float64, device="cuda", generator=gen)
     y = torch.empty_like(x)
     out = {}
-    spmv = lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs)
+    spmv = lambda: B.gs_spmv(ctx, mat, x, y, nrhs=nrhs, variant=spmv_variant)
     sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
     out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, spmv, reps)
     out[NAMES[B.GS_TUNE_SPMV_WS]] = sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
+    if spmv_variant == B.GS_SPMV_ROW_FF and nrhs > 2:
+        out[NAMES[B.GS_TUNE_SPMV_FF_RHS]] = sweep(ctx, B.GS_TUNE_SPMV_FF_RHS, B.GS_K_SPMV, spmv, reps)
     apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
     if fp64:
         out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps)

@@ -25,6 +25,7 @@ GS_ERR_TIMEOUT = -7
 
 GS_SPMV_SRBK = 0
 GS_SPMV_ROW = 1
+GS_SPMV_ROW_FF = 2
 GS_PREC_FP64 = 0
 GS_PREC_FP32 = 1
 GS_PREC_BF16 = 2
@@ -49,7 +50,8 @@ GS_TUNE_BF16_TC = 4
 GS_TUNE_F64_TC = 5
 GS_TUNE_SPMV_WINDOW = 6
 GS_TUNE_SPMV_WS = 7
-GS_TUNE_COUNT = 8
+GS_TUNE_SPMV_FF_RHS = 8
+GS_TUNE_COUNT = 9
 
 K_NAMES = ["assemble", "libprim", "spmv", "mas_levels", "mas_matrices", "mas_invert", "mas_apply_l0",
            "mas_apply_coarse", "pcg_vector", "other"]

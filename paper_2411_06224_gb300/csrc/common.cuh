@@ -84,7 +84,7 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024, 1};  // GS_TUNE_* launch shapes
+  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024, 1, 8};  // GS_TUNE_* launch shapes
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // 256 device bytes: [0] error word, [kSpmvCounterWord] SpMV work counter
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
@@ -166,9 +166,10 @@ int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs,
 int mas_apply_launch_skip(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl,
                           const int* skip);
 // Float-float SpMV (spmv_ff.cu).  ensure_ff builds the matrix's scaled
-// float-float copy once.  spmv_ff_split_launch: y = A x from x already split
-// as xs[k * 3n + i] = (hi, lo) of x * 2^(ff_k[node] - F[k]) (|.| <= 1), F
-// device int[nrhs]; spmv_ff_launch splits x itself (two extra passes).
+// float-float copy once.  spmv_ff_split_launch: y = A x from x already split,
+// node-major across RHS: xs[(node * nrhs + k) * 3 + c] = (hi, lo) of
+// x_k[3 node + c] * 2^(ff_k[node] - F[k]) (|.| <= 1), F device int[nrhs];
+// spmv_ff_launch splits x itself (two extra passes).
 int ensure_ff(gs_ctx ctx, gs_mat m);
 int spmv_ff_split_launch(gs_ctx ctx, gs_mat m, const float2* xs, const int* F, double* y, int nrhs, const int* skip);
 int spmv_ff_launch(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, const int* skip);

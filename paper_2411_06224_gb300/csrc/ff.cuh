@@ -38,4 +38,29 @@ __device__ __forceinline__ float2 ff_split_scaled(double v, int e) {
   return make_float2(h, __double2float_rn(w - (double)h));
 }
 
+// The same split of w = v 2^e without FP64 instructions or conversions (on
+// this part both run on the FP64 pipe): hi is w with its mantissa cut to 24
+// significant bits, so |w - hi| < 2^-23 |w| and lo has w's sign; lo is the
+// remaining 29 bits rounded to 24, made as T - 2^E from bit patterns (T has
+// exponent E and those bits as its fraction; the subtraction is exact, and a
+// rounding carry moves into T's exponent, which stays exact).  Error:
+// |w - hi - lo| <= 2^-47 |w|.  A w below 2^-126 becomes 0, one below 2^-103
+// loses lo; callers choose e so that |w| <= 1.
+__device__ __forceinline__ float2 ff_split_bits(double v, int e) {
+  const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+  const int ef = (int)((hw >> 20) & 0x7ffu);
+  const int fe = ef + e - 896;  // float exponent field of w (double bias 1023, float bias 127)
+  if (ef == 0 || fe <= 0) return make_float2(0.f, 0.f);
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned hb = sign | ((unsigned)min(fe, 254) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+  float lo = 0.f;
+  const int le = fe - 23;
+  if (le > 0) {
+    const unsigned base = sign | ((unsigned)le << 23);
+    const unsigned r = ((lw & 0x1fffffffu) + 32u) >> 6;  // 29 bits rounded to 23, carry included
+    lo = __fsub_rn(__uint_as_float(base + r), __uint_as_float(base));
+  }
+  return make_float2(__uint_as_float(hb), lo);
+}
+
 }  // namespace gs

@@ -298,6 +298,8 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(double* __restrict__ p
 // p = z + beta p (as k_update_p), and the float-float operand of the next
 // SpMV: ps = split(p 2^(k_node - K - F)) with 2^F above |p|, taken from the
 // bounds |z| < 2^fz, |p_old| < 2^fp, |beta| < 2^eb as max(fz, fp + eb) + 1.
+// ps is node-major across right-hand sides, ps[(node * nrhs + k) * 3 + c],
+// so the SpMV gathers all RHS of a column in one contiguous stretch.
 // The blocks also post the exponent bound of the new p, which the last block
 // keeps as fp.  A converged RHS keeps p, ps, fp and fsplit unchanged.
 __global__ void __launch_bounds__(kRedThreads) k_update_p_ff(double* __restrict__ p, const double* __restrict__ z,
@@ -334,7 +336,8 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p_ff(double* __restrict_
           const double v = zv[u] + be * pv[u];
           p[o + j] = v;
           ex = max(ex, ex_bound(v));
-          ps[o + j] = ff_split_scaled(v, kk[j / 3] - F);
+          const uint32_t node = (uint32_t)j / 3u;
+          ps[((int64_t)node * nrhs + k) * 3 + ((uint32_t)j - 3u * node)] = ff_split_bits(v, kk[node] - F);
         }
       }
     }
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p_ff(double* __restrict_
 
 // The first split of p (p = z, |p| < 2^fp): fsplit = fp.
 __global__ void __launch_bounds__(kRedThreads) k_split_p(const double* __restrict__ p, float2* __restrict__ ps,
-                                                         const int32_t* __restrict__ kk, int64_t len,
+                                                         const int32_t* __restrict__ kk, int64_t len, int nrhs,
                                                          PcgScalars* s) {
   const int k = blockIdx.y;
   const int F = s->fp[k] == kExpNone ? 0 : s->fp[k];
@@ -370,7 +373,10 @@ __global__ void __launch_bounds__(kRedThreads) k_split_p(const double* __restric
   const int64_t o = (int64_t)k * len;
   int64_t i0, i1;
   chunk_of(len, i0, i1);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) ps[o + i] = ff_split_scaled(p[o + i], kk[i / 3] - F);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t node = (uint32_t)i / 3u;
+    ps[((int64_t)node * nrhs + k) * 3 + ((uint32_t)i - 3u * node)] = ff_split_bits(p[o + i], kk[node] - F);
+  }
 }
 
 }  // namespace gs
@@ -414,7 +420,7 @@ extern "C" int gs_pcg_solve(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* b,
   GS_TRY(mas_apply_launch(ctx, mas, r, z, nrhs, rl, zl));
   if (ff) {
     { GS_PROF(ctx, GS_K_PCG_VECTOR); k_dot<true, true><<<vg, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit, ipart); }
-    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_split_p<<<vg, kRedThreads, 0, st>>>(p, ps, mat->ff_k, len, s); }
+    { GS_PROF(ctx, GS_K_PCG_VECTOR); k_split_p<<<vg, kRedThreads, 0, st>>>(p, ps, mat->ff_k, len, nrhs, s); }
   } else {
     GS_PROF(ctx, GS_K_PCG_VECTOR);
     k_dot<true><<<vg, kRedThreads, 0, st>>>(r, z, p, len, nrhs, s, partials, kOpRzInit);

@@ -68,25 +68,44 @@ struct LevelIdxNodeMajor {
 // values of each parent's items in ascending lane order and stores the total:
 // every parent has one writer and a fixed order of addition, so the result
 // does not depend on scheduling.  up[a]: the parent of item a (-1: none).
-// Lanes own values v = lane, lane + 32, ... < nv.
+// Lanes own values v = lane, lane + 32, ... < nv; a lane first loads its
+// value of all 32 items (independent loads, one round trip), then sums each
+// parent's members from registers.  The parents' member masks come from
+// __match_any_sync and are shared through shared memory.
 template <typename T, typename Idx>
 __global__ void __launch_bounds__(128) k_restrict_up(const int32_t* __restrict__ up, int32_t n_dom, int N, int nv,
                                                      Idx src, Idx dst, T* __restrict__ rl,
                                                      const int* __restrict__ skip) {
   if (skip && *skip) return;  // every RHS of the solve has converged
+  __shared__ uint32_t gmask[4][32];
+  __shared__ int32_t gpar[4][32];
+  const int w = threadIdx.x >> 5;
   const int32_t d = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (d >= n_dom) return;  // whole warp
   const int32_t par = lane < N ? up[(int64_t)d * N + lane] : -1;
-  uint32_t left = __ballot_sync(kFull, par >= 0);
-  while (left) {
-    const int32_t pp = __shfl_sync(kFull, par, __ffs(left) - 1);
-    const uint32_t g = __ballot_sync(kFull, par == pp);
-    left &= ~g;
-    for (int v = lane; v < nv; v += 32) {
+  const uint32_t realm = __ballot_sync(kFull, par >= 0);
+  const uint32_t same = __match_any_sync(kFull, par);
+  const bool leader = par >= 0 && lane == __ffs(same) - 1;
+  const uint32_t leaders = __ballot_sync(kFull, leader);
+  if (leader) {
+    const int slot = __popc(leaders & ((1u << lane) - 1u));
+    gmask[w][slot] = same;
+    gpar[w][slot] = par;
+  }
+  __syncwarp();
+  const int ng = __popc(leaders);
+  for (int v = lane; v < nv; v += 32) {
+    T val[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) val[j] = ((realm >> j) & 1u) ? rl[src((int64_t)d * N + j, v)] : (T)0;
+    for (int g = 0; g < ng; ++g) {
+      const uint32_t m = gmask[w][g];
       T sum = (T)0;
-      for (uint32_t m = g; m; m &= m - 1) sum += rl[src((int64_t)d * N + (__ffs(m) - 1), v)];
-      rl[dst(pp, v)] = sum;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if ((m >> j) & 1u) sum += val[j];
+      rl[dst(gpar[w][g], v)] = sum;
     }
   }
 }

@@ -53,14 +53,15 @@ def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
                        (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
-                       (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_SPMV_WS, 2), (B.GS_TUNE_COUNT, 2)):
+                       (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_SPMV_WS, 2), (B.GS_TUNE_SPMV_FF_RHS, 3),
+                       (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
             B.gs_tune_set(ctx, param, bad)
     from paper_2411_06224_gb300 import autotune
 
     assert autotune.current(ctx) == {"spmv_lanes": 2, "apply_rhs_per_thread": 4, "spmv32_lanes": 2,
                                      "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1,
-                                     "spmv_row_window": 1024, "spmv_work_stealing": 1}
+                                     "spmv_row_window": 1024, "spmv_work_stealing": 1, "spmv_ff_rhs_per_pass": 8}
 
 
 def test_every_shape_gives_the_oracle_result(B, ctx):
@@ -93,6 +94,28 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
                 else:
                     by_lanes[lanes] = y.clone()
     B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WINDOW, 1024)
+    # the float-float SpMV: every lane count, schedule and RHS-per-thread shape
+    # within its per-row bound, and bitwise the same for a given summation order
+    m = 3.0 * (np.bincount(rid, minlength=V) + np.bincount(cid[rid != cid], minlength=V))
+    ff_bound = np.repeat(((3 * m + 1) * (m + 4) + 6) * 2.0 ** -48, 3) * (bound / 1e-13)
+    ff_by_lanes = {}
+    for ws in autotune.CANDIDATES[B.GS_TUNE_SPMV_WS]:
+        B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WS, ws)
+        for rpp in autotune.CANDIDATES[B.GS_TUNE_SPMV_FF_RHS]:
+            B.gs_tune_set(ctx, B.GS_TUNE_SPMV_FF_RHS, rpp)
+            for lanes in autotune.CANDIDATES[B.GS_TUNE_SPMV_LANES]:
+                B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, lanes)
+                B.gs_spmv(ctx, mat, xd, y, nrhs=nrhs, variant=B.GS_SPMV_ROW_FF)
+                assert np.all(np.abs(y.cpu().numpy() - Ax) <= ff_bound), (ws, rpp, lanes)
+                # with fewer RHS per thread each lane walks all blocks in order:
+                # the one-lane sums
+                key = 1 if rpp < 8 and nrhs > rpp else lanes
+                if key in ff_by_lanes:
+                    assert torch.equal(y, ff_by_lanes[key]), (ws, rpp, lanes)
+                else:
+                    ff_by_lanes[key] = y.clone()
+    B.gs_tune_set(ctx, B.GS_TUNE_SPMV_FF_RHS, 8)
+    B.gs_tune_set(ctx, B.GS_TUNE_SPMV_LANES, 2)
     B.gs_tune_set(ctx, B.GS_TUNE_SPMV_WS, 1)
     zs = {}
     B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 0)  # the RHS-per-thread shape belongs to the FP64-core kernel

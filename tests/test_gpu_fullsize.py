@@ -88,6 +88,19 @@ def test_full_levels_spmv_apply(B, full):
     Aabs = pcg.SymmetricMatrix(V, full["rid"], full["cid"], np.abs(full["au"]))
     for k in range(NRHS):
         assert np.all(np.abs(y[k].cpu().numpy() - A(x[k])) <= 1e-13 * Aabs(np.abs(x[k])))
+    # the float-float product, against its own per-row bound
+    yf = torch.empty_like(y)
+    B.gs_spmv(ctx, full["mat"], dev(x, torch.float64), yf, nrhs=NRHS, variant=B.GS_SPMV_ROW_FF)
+    rid, cid = full["rid"], full["cid"]
+    m = 3.0 * (np.bincount(rid, minlength=V) + np.bincount(cid[rid != cid], minlength=V))
+    gamma = np.repeat(((3 * m + 1) * (m + 4) + 6) * 2.0 ** -48, 3)
+    worst = 0.0
+    for k in range(NRHS):
+        sc = Aabs(np.abs(x[k]))
+        err = np.abs(yf[k].cpu().numpy() - A(x[k]))
+        assert np.all(err <= gamma * sc)
+        worst = max(worst, (err / (1e-13 * sc)).max())
+    print("float-float SpMV at 64^3: max error / (1e-13 |A||x|) =", worst)
     z = torch.empty_like(y)
     B.gs_mas_apply(ctx, full["M"], dev(x, torch.float64), z, nrhs=NRHS)
     z0 = om(x)
@@ -117,6 +130,15 @@ def test_full_pcg_counts_and_residuals(B, full):
     for k in range(NRHS):
         assert abs(int(it[k]) - g[k]) <= 2, (list(it), g)
         assert np.linalg.norm(b[k] - A(xg[k])) <= 1.05e-6 * np.linalg.norm(b[k])
+    # the same solve on the float-float SpMV
+    xf = torch.zeros_like(x)
+    itf, _, _ = B.gs_pcg_solve(ctx, full["mat"], full["M"], dev(b, torch.float64), xf, nrhs=NRHS, tol=1e-6,
+                               variant=B.GS_SPMV_ROW_FF)
+    xfg = xf.cpu().numpy()
+    for k in range(NRHS):
+        assert abs(int(itf[k]) - g[k]) <= 2, (list(itf), g)
+        assert np.linalg.norm(b[k] - A(xfg[k])) <= 1.05e-6 * np.linalg.norm(b[k])
+    print("FP64 SpMV iterations", list(it), "float-float", list(itf), "oracle", g)
     # mixed precision on the same system: the true FP64 residual meets the
     # tolerance.  Both solves stop on a residual test, so their distance is
     # bounded only by cond(A) * 2e-6; it is stated, with a sanity bound.
