@@ -33,18 +33,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300: derived from the nominal 1.25 TFLOP/s FP64 at 2.07 GHz, 152 SMs
-# DRAM bytes of one FP64-core level-0 apply launch per domain at 8 RHS, from
-# an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 40^3
-# case: 172.9 MB over 2000 domains; traffic grows with the domain count.
-APPLY_DRAM_BYTES_PER_DOMAIN_8RHS = 172.9e6 / 2000
-# DRAM bytes per level-0 domain of the digit-split tensor-core apply at 8 RHS,
-# from an ncu capture on the 64^3 case: 1,115.9 MB read + 48.4 MB written over
-# 8,192 domains
-F64TC_DRAM_BYTES_PER_DOMAIN_8RHS = (1115.9e6 + 48.4e6) / 8192
-# DRAM bytes (read + written) of one work-stealing row-SpMV launch on the 64^3
-# sweep system at 8 RHS and the 1024-row order window, by lanes per row, from
-# ncu captures of that case
-SPMV_WS_DRAM_BYTES_64 = {1: 426.5e6 + 75.6e6, 2: 225.2e6 + 39.8e6}
 TOL = 1e-6
 # The headline metric as named for this workload: `value` is the FP64 path's
 # Newton solves/s; the mixed-precision forms are under forms.mixed_precision
@@ -64,7 +52,7 @@ def parse():
                    help="Young's moduli of the step's systems (the named workload: 1e5,1e7,1e9; a single value "
                         "keeps profiling runs small)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    p.add_argument("--spmv", default="row", choices=["row", "srbk", "ff"],
+    p.add_argument("--spmv", default="ff", choices=["row", "srbk", "ff"],
                    help="row: FP64 row gather; srbk: the paper's SRBK; ff: row gather in float-float on the FP32 units")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision form")
@@ -84,6 +72,8 @@ def parse():
                    help="force a launch shape after tuning (names as in config.launch_shapes), e.g. "
                         "spmv_lanes=2; repeatable")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-config1", dest="config1", action="store_false",
+                   help="skip the plain FP64 solve of the 16^3 cube (forms.plain16)")
     p.add_argument("--micro", action="store_true",
                    help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
     p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)  # worker mode
@@ -91,38 +81,123 @@ def parse():
 
 
 # --------------------------------------------------------------------------- oracle sample
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+_ORACLE_SHARED = {}  # set before the pool forks: the children inherit the operators, nothing is pickled
+
+
+def _oracle_pcg_iters(job):
+    """Worker: `iters` oracle PCG iterations on RHS j (forked from the sample
+    process, which never touches a GPU)."""
+    j, iters = job
+    from oracle import pcg
+
+    A, M, bs = _ORACLE_SHARED["A"], _ORACLE_SHARED["M"], _ORACLE_SHARED["b"]
+    t0 = time.perf_counter()
+    pcg.pcg(A, M, bs[j], fixed_iters=iters)
+    return time.perf_counter() - t0
+
+
 def oracle_sample(spec):
     """Time the oracle on bounded samples of the workload (run in a fresh
-    single-threaded process).  Input generation is not timed.  Prints one
-    JSON list with, per sample, the seconds of assembly (t_ga), MAS build
-    (t_pa) and one PCG iteration on one RHS (t_iter)."""
+    process with one BLAS thread per process and no GPU).  Input generation
+    and the once-per-mesh partition are not timed.  Phases per sample:
+    `phases` lists which of "ga" (assembly), "pa" (MAS build) and "pcg" run.
+    PCG: `iters` iterations on one RHS (t_iter), and, with procs > 1, `iters`
+    iterations on each of `procs` RHS in as many concurrent processes
+    (t_iter_par: wall time per iteration, all procs RHS advancing).  Prints
+    one JSON object: the samples and the host."""
     from oracle import assembly, mas, partition, pcg
     from synth.workloads import rhs, stiffness_sweep
 
     systems = stiffness_sweep(Es=tuple(spec["Es"]), n=spec["grid"])
     V = systems[0].n_vertices
     mp, _ = partition.map_remap(partition.recursive_bisection(systems[0].X, 32), 32)  # pre-simulation
-    b = rhs(3 * V, 1)
+    procs = int(spec.get("procs", 1))
+    bs = rhs(3 * V, max(procs, 1))
+    phases = spec.get("phases", ["ga", "pa", "pcg"])
+    cache = {}
     out = []
     for q in range(spec["samples"]):
-        sys_ = systems[q % len(systems)]
+        si = q % len(systems)
+        sys_ = systems[si]
+        ph = phases[q % len(phases)] if spec.get("cycle") else None
+        rec = {"E": sys_.params["E"], "V": V}
+        if ph in (None, "ga") or si not in cache:
+            t0 = time.perf_counter()
+            rid, cid, au = assembly.assemble(sys_.rows, sys_.cols, sys_.blocks)
+            rec["t_ga"] = time.perf_counter() - t0
+            cache[si] = {"asm": (rid, cid, au)}
+        rid, cid, au = cache[si]["asm"]
+        if ph in (None, "pa") or "M" not in cache[si]:
+            t0 = time.perf_counter()
+            M = mas.build_mas(mp, 32, 3, sys_.adj_ptr, sys_.adj, sys_.contacts, rid, cid, au)
+            A = pcg.SymmetricMatrix(V, rid, cid, au)
+            rec["t_pa"] = time.perf_counter() - t0
+            cache[si].update(M=M, A=A)
+        M, A = cache[si]["M"], cache[si]["A"]
+        if ph in (None, "pcg"):
+            k = spec["iters"]
+            t0 = time.perf_counter()
+            pcg.pcg(A, M, bs[0], fixed_iters=k)
+            rec["t_iter"] = (time.perf_counter() - t0) / k
+            rec["k"] = k
+            if procs > 1:
+                import multiprocessing as mpc
+
+                # fork: the children inherit A, M and b; no GPU exists in this process
+                _ORACLE_SHARED.update(A=A, M=M, b=bs)
+                with mpc.get_context("fork").Pool(procs) as pool:
+                    t0 = time.perf_counter()
+                    pool.map(_oracle_pcg_iters, [(j, k) for j in range(procs)], chunksize=1)
+                    rec["t_iter_par"] = (time.perf_counter() - t0) / k
+                rec["procs"] = procs
+        out.append(rec)
+    print(json.dumps({"samples": out, "host": host_info()}))
+
+
+def oracle_full_plain16(spec):
+    """Worker: the oracle's complete Newton solve of the 16^3 plain system
+    (assembly, 2-level MAS build, 4-RHS PCG to 1e-6), `reps` times, single
+    thread; prints per-phase seconds and iteration counts (JSON)."""
+    from oracle import assembly, mas, partition, pcg
+    from synth.workloads import plain_small, rhs
+
+    s_ = plain_small()
+    V = s_.n_vertices
+    mp, _ = partition.map_remap(partition.recursive_bisection(s_.X, 32), 32)
+    b = rhs(3 * V, 4)
+    out = []
+    for _ in range(spec["reps"]):
         t0 = time.perf_counter()
-        rid, cid, au = assembly.assemble(sys_.rows, sys_.cols, sys_.blocks)
+        rid, cid, au = assembly.assemble(s_.rows, s_.cols, s_.blocks)
         t1 = time.perf_counter()
-        M = mas.build_mas(mp, 32, 3, sys_.adj_ptr, sys_.adj, sys_.contacts, rid, cid, au)
+        M = mas.build_mas(mp, 32, 2, s_.adj_ptr, s_.adj, s_.contacts, rid, cid, au)
         A = pcg.SymmetricMatrix(V, rid, cid, au)
         t2 = time.perf_counter()
-        pcg.pcg(A, M, b, fixed_iters=spec["iters"])
+        _, it, _ = pcg.pcg(A, M, b, tol=1e-6)
         t3 = time.perf_counter()
-        out.append({"E": sys_.params["E"], "t_ga": t1 - t0, "t_pa": t2 - t1, "t_iter": (t3 - t2) / spec["iters"],
-                    "k": spec["iters"], "V": V})
-    print(json.dumps(out))
+        out.append({"t_ga": t1 - t0, "t_pa": t2 - t1, "t_pcg": t3 - t2, "iters": [int(v) for v in it]})
+    print(json.dumps({"samples": out, "host": host_info()}))
 
 
-def run_oracle_sample(grid, Es, samples, iters=3):
+def run_oracle_sample(grid, Es, samples, iters=20, procs=1, cycle=False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    spec = json.dumps({"grid": grid, "Es": list(Es), "samples": samples, "iters": iters})
+    spec = json.dumps({"grid": grid, "Es": list(Es), "samples": samples, "iters": iters, "procs": procs,
+                       "cycle": cycle})
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec], env=env,
                        capture_output=True, text=True, timeout=3600)
     if r.returncode != 0:
@@ -130,10 +205,14 @@ def run_oracle_sample(grid, Es, samples, iters=3):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_rate(sample, iters_per_solve):
-    """Newton solves/s of the oracle: T_ga + T_pa + (PCG iterations summed over the RHS) * T_iter."""
-    t = sample["t_ga"] + sample["t_pa"] + iters_per_solve * sample["t_iter"]
-    return 1.0 / t, t
+def oracle_rates(t_ga, t_pa, t_iter, t_iter_par, iters):
+    """Newton solves/s of the oracle for per-RHS PCG iteration counts `iters`:
+    single thread T = T_ga + T_pa + sum_k iters_k T_iter (supplement Eq. 1);
+    with the RHS in concurrent processes T = T_ga + T_pa + max_k iters_k
+    T_iter_par (assembly and build stay single-threaded, as the oracle is)."""
+    t1 = t_ga + t_pa + sum(iters) * t_iter
+    tp = t_ga + t_pa + max(iters) * t_iter_par if t_iter_par else None
+    return 1.0 / t1, (1.0 / tp if tp else None), t1, tp
 
 
 # --------------------------------------------------------------------------- clocks
@@ -198,10 +277,211 @@ def make_workload(grid, nrhs, rank, Es=(1e5, 1e7, 1e9)):
     return systems, np.ascontiguousarray(b)
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` as recorded from an ncu
+    capture in profiles/dram_traffic.md, if the kernel's source file still has
+    the hash recorded with it (else None: the kernel changed since)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) < 5 or cells[0] != kernel or cells[1] != workload:
+            continue
+        src = os.path.join(ROOT, cells[2])
+        if not os.path.exists(src):
+            return None
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != cells[3]:
+            return None
+        return float(cells[4])
+    return None
+
+
+def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live, alone, workload=None):
+    """Roofline lines of the level-0 MAS apply and the SpMV: algorithmic bytes
+    (or operations) per launch over the mean CUDA-event launch time, `live`
+    (launches, ms per class) inside the timed region and `alone` from a
+    sequential per-class step."""
+    import numpy as np
+    import torch
+
+    launches, kms = live
+    launches_1, ms_1 = alone
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    fp64_peak_tflops = sms * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    ld = 3 * N
+    n_dom0 = ndom
+    real0 = np.bincount(mp // N, minlength=n_dom0)
+    apply_flops = 2.0 * float(np.sum((3 * real0) ** 2)) * nrhs
+    inv_bytes = (8 if prec == B.GS_PREC_FP64 else 4) * n_dom0 * ld * ld
+    apply_bytes = inv_bytes + 2 * 8 * 3 * V * nrhs
+    n_off = nnzb - V
+    spmv_flops = nrhs * (18.0 * V + 36.0 * n_off)
+    spmv_bytes = 76.0 * nnzb + 4.0 * (V + 1) + 2 * 8 * 3 * V * nrhs
+    t_apply = kms[B.GS_K_MAS_APPLY_L0] / 1e3 / max(launches[B.GS_K_MAS_APPLY_L0], 1)
+    t_spmv = kms[B.GS_K_SPMV] / 1e3 / max(launches[B.GS_K_SPMV], 1)
+    t_apply_iso = ms_1[B.GS_K_MAS_APPLY_L0] / 1e3 / max(launches_1[B.GS_K_MAS_APPLY_L0], 1)
+    t_spmv_iso = ms_1[B.GS_K_SPMV] / 1e3 / max(launches_1[B.GS_K_SPMV], 1)
+    traffic_key = f"{workload},{nrhs}rhs" if workload else None
+
+    def fp64_line(flops, nbytes, tsec, traffic):
+        return {"bound": "alu", "achieved": flops / tsec / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": flops / tsec / 1e12 / fp64_peak_tflops, "traffic": traffic,
+                "hbm_gbs": nbytes / tsec / 1e9, "hbm_frac": nbytes / tsec / 1e9 / hbm,
+                "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
+
+    f64tc = (prec == B.GS_PREC_FP64 and nrhs <= 8 and ld % 16 == 0 and B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 1)
+    if f64tc:
+        # FP64-accurate apply on the BF16 tensor cores: the 7 BF16 digit matrices
+        # of every level-0 inverse (14 B per entry) stream from HBM once per apply,
+        # plus r read and z written (FP64)
+        dig_bytes = 7 * 2 * n_dom0 * ld * ld
+        tc_bytes = dig_bytes + 2 * 8 * 3 * V * nrhs
+        traffic = recorded_traffic("k_level0_f64tc", traffic_key) if traffic_key else None
+        apply_line = {"bound": "hbm", "achieved": tc_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": tc_bytes / t_apply / 1e9 / hbm, "traffic": traffic,
+                      "method_bytes_frac": apply_bytes / t_apply / 1e9 / hbm,
+                      "fp64_equivalent_tflops": apply_flops / t_apply / 1e12,
+                      "fp64_equivalent_frac_of_fp64_peak": apply_flops / t_apply / 1e12 / fp64_peak_tflops,
+                      "flops_per_launch": apply_flops, "bytes_per_launch": tc_bytes,
+                      "method_bytes_per_launch": apply_bytes, "avg_launch_ms": t_apply * 1e3,
+                      "kernel": "k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
+                                "splitting on tcgen05, + prolongation)"}
+        apply_iso_ach = tc_bytes / t_apply_iso / 1e9
+    else:
+        apply_line = fp64_line(apply_flops, apply_bytes, t_apply, None)
+        apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
+                                "(level-0 MAS apply + prolongation)")
+        apply_iso_ach = apply_flops / t_apply_iso / 1e12
+    apply_line["isolated"] = {"avg_launch_ms": t_apply_iso * 1e3, "achieved": apply_iso_ach,
+                              "frac": apply_iso_ach / apply_line["peak"]}
+    spmv_ws = spmv in ("row", "ff") and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WS) == 1
+    if spmv == "ff":
+        # float-float on the FP32 units: 12 FP32 instructions per term (exact
+        # product, two-sum, small parts), 9 terms per block use and RHS, one use
+        # per diagonal block and two per off-diagonal block
+        ff_inst = nrhs * 9 * 12.0 * (V + 2.0 * n_off)
+        fp32_peak = sms * 128 * sm_mhz_max * 1e6 / 1e12  # T FP32 instructions/s
+        kname = "k_spmv_ff_ws" if spmv_ws else "k_spmv_ff_row"
+        spmv_line = {"bound": "alu", "achieved": ff_inst / t_spmv / 1e12, "peak": fp32_peak,
+                     "unit": "T FP32 instructions/s", "frac": ff_inst / t_spmv / 1e12 / fp32_peak,
+                     "traffic": (recorded_traffic(kname, f"{traffic_key},ff_rhs{B.gs_tune_get(ctx, B.GS_TUNE_SPMV_FF_RHS)}")
+                                 if traffic_key else None),
+                     "hbm_gbs": spmv_bytes / t_spmv / 1e9, "hbm_frac": spmv_bytes / t_spmv / 1e9 / hbm,
+                     "fp64_equivalent_tflops": spmv_flops / t_spmv / 1e12,
+                     "fp64_equivalent_frac_of_fp64_peak": spmv_flops / t_spmv / 1e12 / fp64_peak_tflops,
+                     "instructions_per_launch": ff_inst, "flops_per_launch": spmv_flops,
+                     "bytes_per_launch": spmv_bytes, "avg_launch_ms": t_spmv * 1e3, "kernel": kname}
+        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3, "achieved": ff_inst / t_spmv_iso / 1e12,
+                                 "frac": ff_inst / t_spmv_iso / 1e12 / fp32_peak,
+                                 "hbm_frac": spmv_bytes / t_spmv_iso / 1e9 / hbm}
+    else:
+        kname = "k_spmv_row_ws" if spmv_ws else f"k_spmv_{spmv}"
+        spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv,
+                              recorded_traffic(kname, traffic_key) if traffic_key else None)
+        spmv_line["kernel"] = kname
+        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3, "achieved": spmv_flops / t_spmv_iso / 1e12,
+                                 "frac": spmv_flops / t_spmv_iso / 1e12 / fp64_peak_tflops}
+    return apply_line, spmv_line
+
+
+def config1_form(args, B, dev, variant, clk):
+    """The plain FP64 solve on the 16^3 cube (4,096 vertices, 2,000 random
+    contacts, E = 1e5, 4 RHS, 2-level MAS with 32-node domains, tol 1e-6):
+    Newton solves/s through the whole path on one stream, the kernels'
+    roofline lines, and the oracle's complete solve timed on the host."""
+    import numpy as np
+    import torch
+
+    from synth.workloads import plain_small, rhs
+
+    s_ = plain_small()
+    V, N, L, K = s_.n_vertices, 32, 2, 4
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    mp, nd = B.gs_partition(s_.X, N)
+    d = dict(rows=t(s_.rows, torch.int32), cols=t(s_.cols, torch.int32),
+             blocks=t(s_.blocks.reshape(-1, 3, 3), torch.float64), map=t(mp, torch.int32),
+             adj_ptr=t(s_.adj_ptr, torch.int32), adj=t(s_.adj, torch.int32), contacts=t(s_.contacts, torch.int32))
+    b = t(rhs(3 * V, K), torch.float64)
+    x = torch.zeros_like(b)
+    ctx = B.gs_create(dev.index or 0, torch.cuda.current_stream())
+
+    def solve():
+        mat = B.gs_assemble(ctx, V, d["rows"], d["cols"], d["blocks"])
+        mas = B.gs_build_mas(ctx, mat, d["map"], nd, d["adj_ptr"], d["adj"], d["contacts"], domain_size=N,
+                             max_levels=L)
+        it, _, _ = B.gs_pcg_solve(ctx, mat, mas, b, x, nrhs=K, tol=TOL, max_iter=20000, variant=variant)
+        info = B.gs_mat_info(mat)[1]
+        B.gs_mas_destroy(mas)
+        B.gs_mat_destroy(mat)
+        return it, info
+
+    try:
+        for _ in range(max(args.warmup, 3)):
+            it, nnzb = solve()
+        B.gs_profile_begin(ctx, range(B.GS_K_COUNT))
+        solve()
+        alone = B.gs_profile_end(ctx)
+        steps = 20
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.gs_profile_begin(ctx, [B.GS_K_MAS_APPLY_L0, B.GS_K_SPMV])
+        e0.record()
+        for _ in range(steps):
+            it, _ = solve()
+        e1.record()
+        torch.cuda.synchronize()
+        live = B.gs_profile_end(ctx)
+        sec = e0.elapsed_time(e1) / 1e3
+        apply_line, spmv_line = kernel_lines(B, ctx, dev, clk, "ff" if variant == B.GS_SPMV_ROW_FF else "row",
+                                             B.GS_PREC_FP64, K, N, V, nnzb, nd, mp, live, alone)
+        dominant = apply_line if live[1][B.GS_K_MAS_APPLY_L0] >= live[1][B.GS_K_SPMV] else spmv_line
+        out = {"workload": "tet cube 16^3 (4096 vertices), E=1e5, 2000 random contacts, 4 RHS, 2-level MAS N=32, "
+                           "PCG tol 1e-6, one stream", "value": steps / sec, "unit": "Newton solves/s",
+                "ms_per_solve": sec / steps * 1e3, "steps": steps, "pcg_iterations": [int(v) for v in it],
+                "roofline": dominant, "kernels": {"mas_apply_l0": apply_line, "spmv": spmv_line},
+                "phase_ms_one_solve": {B.K_NAMES[k]: float(alone[1][k]) for k in range(B.GS_K_COUNT)}}
+    finally:
+        B.gs_destroy(ctx)
+    if not args.no_cpu_baseline:
+        try:
+            env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                       CUDA_VISIBLE_DEVICES="")
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                                json.dumps({"kind": "plain16", "reps": 3})], env=env, capture_output=True, text=True,
+                               timeout=1800)
+            res = json.loads(r.stdout.strip().splitlines()[-1])
+            smp = res["samples"][-1]
+            tot = smp["t_ga"] + smp["t_pa"] + smp["t_pcg"]
+            out["cpu_baseline"] = {
+                "value": 1.0 / tot, "unit": "Newton solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"the FP64 numpy/scipy oracle's complete solve of this system on one host core "
+                           f"({res['host']['cpu_model']}): assembly {smp['t_ga']:.3f} s, 2-level MAS build "
+                           f"{smp['t_pa']:.3f} s, PCG {smp['t_pcg']:.3f} s (iterations {smp['iters']}); last of 3"),
+                "host": res["host"]}
+        except Exception as e:  # noqa: BLE001
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
+    return out
+
+
 def main():
     args = parse()
     if args.oracle_sample:
-        oracle_sample(json.loads(args.oracle_sample))
+        spec = json.loads(args.oracle_sample)
+        if spec.get("kind") == "plain16":
+            oracle_full_plain16(spec)
+        else:
+            oracle_sample(spec)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -666,94 +946,18 @@ def main():
             "graph": "whole PCG loop = one CUDA graph launch (conditional WHILE node)",
         }
 
+    # the plain FP64 solve on the 16^3 cube
+    plain16 = None
+    if args.config1:
+        try:
+            plain16 = config1_form(args, B, dev, variant, clk)
+        except B.GsError as e:
+            plain16 = {"error": str(e)[:300]}
+
     # roofline of the dominant kernel class
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    fp64_peak_tflops = sms * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    ld = 3 * N
-    n_dom0 = ndom
-    real0 = np.bincount(mp // N, minlength=n_dom0)
-    apply_flops = 2.0 * float(np.sum((3 * real0) ** 2)) * args.nrhs
-    inv_bytes = (8 if prec == B.GS_PREC_FP64 else 4) * n_dom0 * ld * ld
-    apply_bytes = inv_bytes + 2 * 8 * 3 * V * args.nrhs
-    n_off = nnzb - V
-    spmv_flops = args.nrhs * (18.0 * V + 36.0 * n_off)
-    spmv_bytes = 76.0 * nnzb + 4.0 * (V + 1) + 2 * 8 * 3 * V * args.nrhs
-    k_apply = launches[B.GS_K_MAS_APPLY_L0]
-    k_spmv = launches[B.GS_K_SPMV]
-    t_apply = kms[B.GS_K_MAS_APPLY_L0] / 1e3 / max(k_apply, 1)
-    t_spmv = kms[B.GS_K_SPMV] / 1e3 / max(k_spmv, 1)
-    # the same kernels timed alone (the sequential per-class step): with the
-    # systems on concurrent streams, the live durations include the overlap
-    t_apply_iso = ms_1[B.GS_K_MAS_APPLY_L0] / 1e3 / max(launches_1[B.GS_K_MAS_APPLY_L0], 1)
-    t_spmv_iso = ms_1[B.GS_K_SPMV] / 1e3 / max(launches_1[B.GS_K_SPMV], 1)
-
-    def fp64_line(flops, nbytes, tsec, traffic):
-        return {"bound": "alu", "achieved": flops / tsec / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": flops / tsec / 1e12 / fp64_peak_tflops, "traffic": traffic,
-                "hbm_gbs": nbytes / tsec / 1e9, "hbm_frac": nbytes / tsec / 1e9 / hbm,
-                "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
-
-    f64tc = (prec == B.GS_PREC_FP64 and args.nrhs <= 8 and ld % 16 == 0
-             and B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 1)
-    if f64tc:
-        # FP64-accurate apply on the BF16 tensor cores: the 7 BF16 digit matrices
-        # of every level-0 inverse (14 B per entry) stream from HBM once per apply,
-        # plus r read and z written (FP64), plus the coarse z read once per node
-        dig_bytes = 7 * 2 * n_dom0 * ld * ld
-        tc_bytes = dig_bytes + 2 * 8 * 3 * V * args.nrhs
-        traffic = (F64TC_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
-                   if args.nrhs == 8 and N == 32 and F64TC_DRAM_BYTES_PER_DOMAIN_8RHS else None)
-        apply_line = {"bound": "hbm", "achieved": tc_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": tc_bytes / t_apply / 1e9 / hbm, "traffic": traffic,
-                      "fp64_equivalent_tflops": apply_flops / t_apply / 1e12,
-                      "fp64_equivalent_frac_of_fp64_peak": apply_flops / t_apply / 1e12 / fp64_peak_tflops,
-                      "flops_per_launch": apply_flops, "bytes_per_launch": tc_bytes, "avg_launch_ms": t_apply * 1e3,
-                      "kernel": "k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
-                                "splitting on tcgen05, + prolongation)"}
-    else:
-        traffic = (APPLY_DRAM_BYTES_PER_DOMAIN_8RHS * n_dom0
-                   if args.nrhs == 8 and prec == B.GS_PREC_FP64 and N == 32
-                   and B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS) == 4 else None)  # the captured shape
-        apply_line = fp64_line(apply_flops, apply_bytes, t_apply, traffic)
-        apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
-                                "(level-0 MAS apply + prolongation)")
-    spmv_ws = args.spmv in ("row", "ff") and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WS) == 1
-    if args.spmv == "ff":
-        # float-float on the FP32 units: 12 FP32 instructions per term (exact
-        # product, two-sum, small parts), 9 terms per block use and RHS, one use
-        # per diagonal block and two per off-diagonal block
-        ff_inst = args.nrhs * 9 * 12.0 * (V + 2.0 * n_off)
-        fp32_peak = sms * 128 * sm_mhz_max * 1e6 / 1e12  # T FP32 instructions/s
-        spmv_line = {"bound": "alu", "achieved": ff_inst / t_spmv / 1e12, "peak": fp32_peak,
-                     "unit": "T FP32 instructions/s", "frac": ff_inst / t_spmv / 1e12 / fp32_peak, "traffic": None,
-                     "hbm_gbs": spmv_bytes / t_spmv / 1e9, "hbm_frac": spmv_bytes / t_spmv / 1e9 / hbm,
-                     "fp64_equivalent_tflops": spmv_flops / t_spmv / 1e12,
-                     "fp64_equivalent_frac_of_fp64_peak": spmv_flops / t_spmv / 1e12 / fp64_peak_tflops,
-                     "instructions_per_launch": ff_inst, "flops_per_launch": spmv_flops,
-                     "bytes_per_launch": spmv_bytes, "avg_launch_ms": t_spmv * 1e3}
-        spmv_line["kernel"] = "k_spmv_ff_ws" if spmv_ws else "k_spmv_ff_row"
-        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
-                                 "achieved": ff_inst / t_spmv_iso / 1e12,
-                                 "frac": ff_inst / t_spmv_iso / 1e12 / fp32_peak,
-                                 "hbm_frac": spmv_bytes / t_spmv_iso / 1e9 / hbm}
-    else:
-        spmv_traffic = (SPMV_WS_DRAM_BYTES_64.get(B.gs_tune_get(ctx, B.GS_TUNE_SPMV_LANES))
-                        if spmv_ws and args.grid == 64 and args.nrhs == 8
-                        and B.gs_tune_get(ctx, B.GS_TUNE_SPMV_WINDOW) == 1024 else None)  # the captured shapes
-        spmv_line = fp64_line(spmv_flops, spmv_bytes, t_spmv, spmv_traffic)
-        spmv_line["kernel"] = "k_spmv_row_ws" if spmv_ws else f"k_spmv_{args.spmv}"
-        # alone: the same arithmetic over the sequential step's durations
-        spmv_line["isolated"] = {"avg_launch_ms": t_spmv_iso * 1e3,
-                                 "achieved": spmv_flops / t_spmv_iso / 1e12,
-                                 "frac": spmv_flops / t_spmv_iso / 1e12 / fp64_peak_tflops}
-    apply_iso_ach = (tc_bytes / t_apply_iso / 1e9) if f64tc else (apply_flops / t_apply_iso / 1e12)
-    apply_line["isolated"] = {"avg_launch_ms": t_apply_iso * 1e3, "achieved": apply_iso_ach,
-                              "frac": apply_iso_ach / apply_line["peak"]}
+    apply_line, spmv_line = kernel_lines(B, ctx, dev, clk, args.spmv, prec, args.nrhs, N, V, nnzb, ndom, mp,
+                                         (launches, kms), (launches_1, ms_1),
+                                         workload="tet64" if args.grid == 64 else None)
     for ln in (apply_line, spmv_line):
         ln["concurrent_streams"] = n_lanes
     dominant = apply_line if kms[B.GS_K_MAS_APPLY_L0] >= kms[B.GS_K_SPMV] else spmv_line
@@ -793,7 +997,7 @@ def main():
         "phase_ms_one_step": {B.K_NAMES[k]: float(ms_1[k]) for k in range(B.GS_K_COUNT)},
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
-        "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth},
+        "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth, "plain16": plain16},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),
@@ -801,15 +1005,27 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            smp = run_oracle_sample(args.grid, [1e5], 1)[0]
-            mean_iters = float(np.mean([sum(i) for i in iters]))
-            rate, tsolve = oracle_rate(smp, mean_iters)
+            res = run_oracle_sample(args.grid, [1e5], 1, iters=20, procs=args.nrhs)
+            smp, host = res["samples"][0], res["host"]
+            T1 = Tp = 0.0
+            for its in iters:  # the step's systems, with the GPU run's per-RHS counts
+                _, _, t1, tp = oracle_rates(smp["t_ga"], smp["t_pa"], smp["t_iter"], smp.get("t_iter_par"), its)
+                T1 += t1
+                Tp += tp if tp else t1
+            rate1, ratep = len(iters) / T1, len(iters) / Tp
             line["cpu_baseline"] = {
-                "value": rate, "unit": "Newton solves/s", "cores": 1, "kind": "oracle",
-                "sample": (f"FP64 numpy/scipy oracle, single thread, on the E=1e5 system: full assembly "
-                           f"({smp['t_ga']:.1f} s), full 3-level MAS build ({smp['t_pa']:.1f} s), {smp['k']} PCG "
-                           f"iterations on 1 RHS ({smp['t_iter']:.3f} s each); solve time extrapolated with the "
-                           f"GPU run's mean PCG iterations summed over the {args.nrhs} RHS ({mean_iters:.0f})"),
+                "value": ratep, "unit": "Newton solves/s", "cores": smp.get("procs", 1), "kind": "oracle",
+                "sample": (f"FP64 numpy/scipy oracle on the host ({host['nproc']} cores, {host['cpu_model']}), one BLAS "
+                           f"thread per process, E=1e5 system of the {args.grid}^3 sweep: full assembly "
+                           f"({smp['t_ga']:.2f} s), full 3-level MAS build ({smp['t_pa']:.2f} s), {smp['k']} PCG "
+                           f"iterations on 1 RHS ({smp['t_iter']:.3f} s each) and on {smp.get('procs', 1)} RHS in as "
+                           f"many concurrent processes ({smp.get('t_iter_par', 0):.3f} s per iteration); a step's "
+                           f"three solves timed with the GPU run's per-RHS iteration counts, RHS in parallel "
+                           f"(assembly and build single-threaded)"),
+                "single_thread": {"value": rate1, "cores": 1},
+                "phases_s": {"assembly": smp["t_ga"], "mas_build": smp["t_pa"], "pcg_iteration_1rhs": smp["t_iter"],
+                             "pcg_iteration_parallel": smp.get("t_iter_par")},
+                "host": host,
             }
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
@@ -912,22 +1128,42 @@ def micro(args):
 
 
 def reference_arm(args, rank, world):
-    """The oracle timed on the host cores (rank 0 only), same metric and workload."""
+    """The oracle timed on the host cores (rank 0 only), same metric and workload.
+
+    A step is one bounded phase sample of the workload, cycling through
+    assembly, MAS build and PCG (20 iterations on 1 RHS, then on every RHS in
+    as many concurrent processes); `value` combines the timed steps' mean
+    phase times with the oracle's own per-RHS iteration counts of the three
+    systems (supplement Eq. 1), RHS in parallel.  `ms_per_step` is the wall
+    time of a step."""
     if rank != 0:
         return
     import json as _json
 
     golden = os.path.join(ROOT, "tests", "golden", "sweep64_pcg_iterations.json")
-    iters = None
-    if os.path.exists(golden):
-        g = _json.load(open(golden))
-        iters = float(sum(sum(v) for v in g["iterations"].values()) / len(g["iterations"]))
-    Es = (1e5, 1e7, 1e9)
-    allv = run_oracle_sample(args.grid, Es, args.warmup + args.steps, iters=2)
+    its = None
+    if args.grid == 64 and os.path.exists(golden):
+        its = list(_json.load(open(golden))["iterations"].values())
+    n_contacts = max(1, 200_000 * args.grid ** 3 // 64 ** 3)
+    Es = [float(e) for e in args.sweep.split(",")]
+    res = run_oracle_sample(args.grid, Es, args.warmup + args.steps, iters=20, procs=args.nrhs, cycle=True)
+    allv, host = res["samples"], res["host"]
     vals = allv[args.warmup:] or allv[-1:]
-    n_it = iters if iters is not None else 8 * 150.0
-    rates = [oracle_rate(v, n_it)[0] for v in vals]
-    value = statistics.mean(rates)
+    mean = lambda key: statistics.mean([v[key] for v in vals if v.get(key) is not None] or
+                                      [v[key] for v in allv if v.get(key) is not None])
+    t_ga, t_pa, t_it, t_par = mean("t_ga"), mean("t_pa"), mean("t_iter"), mean("t_iter_par")
+    if its is None:
+        its = [[150] * args.nrhs] * len(Es)
+    T1 = sum(oracle_rates(t_ga, t_pa, t_it, t_par, v)[2] for v in its)
+    Tp = sum(oracle_rates(t_ga, t_pa, t_it, t_par, v)[3] for v in its)
+    value = len(its) / Tp
+    step_wall = []
+    for v in vals:
+        w = v.get("t_ga", 0.0) if "k" not in v else 0.0
+        w += v.get("t_pa", 0.0) if "k" not in v else 0.0
+        if "k" in v:
+            w = v["k"] * (v["t_iter"] + v.get("t_iter_par", 0.0))
+        step_wall.append(w)
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -936,18 +1172,25 @@ def reference_arm(args, rank, world):
         "n_gpus": world,
         "steps": len(vals),
         "warmup": args.warmup,
-        "ms_per_step": 1e3 / value,
+        "ms_per_step": 1e3 * statistics.mean(step_wall),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"tet cube {args.grid}^3 stiffness sweep E=1e5,1e7,1e9; 8 RHS; 3-level MAS N=32; PCG tol 1e-6"},
-        "cpu_baseline": {"value": value, "unit": "Newton solves/s", "cores": 1, "kind": "oracle",
-                         "sample": ("FP64 numpy/scipy oracle, single thread: per step full assembly + full MAS build "
-                                    "+ 2 PCG iterations on 1 RHS of one system (E cycles 1e5, 1e7, 1e9); solve time "
-                                    "extrapolated with the oracle's own iteration counts summed over 8 RHS "
-                                    + ("(tests/golden/sweep64_pcg_iterations.json)" if iters else "(assumed 150 per RHS)"))},
+        "config": {"workload": f"tet cube {args.grid}^3 stiffness sweep E={args.sweep}; {n_contacts} contacts; "
+                               f"{args.nrhs} RHS; 3-level MAS N=32; PCG tol 1e-6",
+                   "step": "one phase sample of the workload (assembly, MAS build, or 20 PCG iterations on 1 RHS "
+                           f"and on {args.nrhs} RHS in concurrent processes), cycling"},
+        "cpu_baseline": {"value": value, "unit": "Newton solves/s", "cores": args.nrhs, "kind": "oracle",
+                         "sample": (f"FP64 numpy/scipy oracle on {host['nproc']} host cores ({host['cpu_model']}), one "
+                                    f"BLAS thread per process: mean phase times assembly {t_ga:.2f} s, MAS build "
+                                    f"{t_pa:.2f} s, PCG iteration {t_it:.3f} s (1 RHS) / {t_par:.3f} s ({args.nrhs} RHS "
+                                    f"in parallel processes); solves timed with the oracle's own per-RHS iteration "
+                                    + ("counts (tests/golden/sweep64_pcg_iterations.json)" if args.grid == 64
+                                       else "counts assumed 150 per RHS")),
+                         "single_thread": {"value": len(its) / T1, "cores": 1},
+                         "host": host},
         "e2e": {"value": value, "unit": "Newton solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

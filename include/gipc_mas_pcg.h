@@ -313,7 +313,7 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
                                      group per row */
 #define GS_TUNE_SPMV_FF_RHS 8     /* float-float SpMV (GS_SPMV_ROW_FF): right-hand sides per thread and pass,
                                      8 (default; the GS_TUNE_SPMV_LANES lanes of a row share its blocks), or
-                                     4 / 2 (each of nrhs / value lanes walks all the row's blocks for its own
+                                     4 / 2 / 1 (each of nrhs / value lanes walks all the row's blocks for its own
                                      right-hand sides; fewer registers, more resident warps) */
 #define GS_TUNE_COUNT 9           /* number of parameters */
 int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value);

@@ -45,7 +45,7 @@ CANDIDATES = {
     B.GS_TUNE_F64_TC: (1, 2, 0),
     B.GS_TUNE_SPMV_WINDOW: (0, 256, 1024, 4096, 16384),
     B.GS_TUNE_SPMV_WS: (0, 1),
-    B.GS_TUNE_SPMV_FF_RHS: (8, 4, 2),
+    B.GS_TUNE_SPMV_FF_RHS: (8, 4, 2, 1),
 }
 
 NAMES = {
@@ -116,7 +116,7 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
     out[NAMES[B.GS_TUNE_SPMV_LANES]] = sweep(ctx, B.GS_TUNE_SPMV_LANES, B.GS_K_SPMV, spmv, reps)
     out[NAMES[B.GS_TUNE_SPMV_WS]] = sweep(ctx, B.GS_TUNE_SPMV_WS, B.GS_K_SPMV, spmv, reps)
-    if spmv_variant == B.GS_SPMV_ROW_FF and nrhs > 2:
+    if spmv_variant == B.GS_SPMV_ROW_FF and nrhs > 1:
         out[NAMES[B.GS_TUNE_SPMV_FF_RHS]] = sweep(ctx, B.GS_TUNE_SPMV_FF_RHS, B.GS_K_SPMV, spmv, reps)
     apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
     if fp64:

@@ -345,7 +345,7 @@ int spmv_ff_split_launch(gs_ctx ctx, gs_mat m, const float2* xs, const int* F, d
   GS_TRY(ensure_ff(ctx, m));
   const int64_t stride = 3LL * m->n;
   // GS_TUNE_SPMV_FF_RHS = 8: lanes (GS_TUNE_SPMV_LANES) stride over a row's
-  // blocks, 8 RHS per pass (4 with 8 lanes).  4 or 2: each lane walks all
+  // blocks, 8 RHS per pass (4 with 8 lanes).  4, 2 or 1: each lane walks all
   // blocks for its own RHS groups of that size, nrhs / size lanes per row
   // (a power of two, at most 8).
   const int rpp = ctx->tune[GS_TUNE_SPMV_FF_RHS];
@@ -360,7 +360,7 @@ int spmv_ff_split_launch(gs_ctx ctx, gs_mat m, const float2* xs, const int* F, d
   const bool ws = ctx->tune[GS_TUNE_SPMV_WS] && ctx->sm_count > 0;
   int* counter = ctx->d_flags + kSpmvCounterWord;
   if (ws) GS_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
-  const int per_sm = split ? (rpp == 4 ? 3 : 4) : (nrhs == 1 ? 4 : (lanes == 8 ? 3 : 2));
+  const int per_sm = split ? (rpp == 4 ? 3 : 4) : (nrhs == 1 ? 4 : (lanes == 8 ? 3 : 2));  // ff_blocks_per_sm
   const int wgrid = std::min(grid, per_sm * std::max(ctx->sm_count, 1));
 #define GS_FF_ARGS \
   m->row_order, m->row_ptr, m->cid, m->lo_ptr, m->lo_idx, m->lo_col, m->au_ff, m->ff_k, m->n, stride, nrhs, xs, F, y
@@ -378,10 +378,14 @@ int spmv_ff_split_launch(gs_ctx ctx, gs_mat m, const float2* xs, const int* F, d
         if (lanes == 2) GS_FF_LAUNCH(2, 4, true);
         else if (lanes == 4) GS_FF_LAUNCH(4, 4, true);
         else GS_FF_LAUNCH(8, 4, true);
-      } else {
+      } else if (rpp == 2) {
         if (lanes == 2) GS_FF_LAUNCH(2, 2, true);
         else if (lanes == 4) GS_FF_LAUNCH(4, 2, true);
         else GS_FF_LAUNCH(8, 2, true);
+      } else {
+        if (lanes == 2) GS_FF_LAUNCH(2, 1, true);
+        else if (lanes == 4) GS_FF_LAUNCH(4, 1, true);
+        else GS_FF_LAUNCH(8, 1, true);
       }
     } else if (nrhs == 1) {
       if (lanes == 8) GS_FF_LAUNCH(8, 1, false);

@@ -77,7 +77,7 @@ def _spmv(B, ctx, mat, x, variant):
 @pytest.mark.parametrize("name", ["cube8", "cube11"])
 @pytest.mark.parametrize("nrhs", [1, 3, 8, 12])
 @pytest.mark.parametrize("lanes,ws,rpp", [(1, 1, 8), (2, 1, 8), (4, 1, 8), (8, 1, 8), (2, 0, 8), (2, 1, 4), (2, 1, 2),
-                                          (2, 0, 2)])
+                                          (2, 0, 2), (2, 1, 1)])
 def test_ff_spmv_within_its_bound(B, ctx, name, nrhs, lanes, ws, rpp):
     s = case(name)
     V = s.n_vertices
