@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--sweep", default="1e5,1e7,1e9",
                    help="Young's moduli of the step's systems (the named workload: 1e5,1e7,1e9; a single value "
                         "keeps profiling runs small)")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
+                   help="preconditioner storage of the main path (FP64 PCG throughout)")
     p.add_argument("--spmv", default="ff", choices=["row", "srbk", "ff"],
                    help="row: FP64 row gather; srbk: the paper's SRBK; ff: row gather in float-float on the FP32 units")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -507,7 +508,7 @@ def main():
     systems, b_host = make_workload(args.grid, args.nrhs, rank, Es=[float(e) for e in args.sweep.split(",")])
     V = systems[0].n_vertices
     N, L = 32, 3
-    prec = B.GS_PREC_FP32 if args.precision == "fp32" else B.GS_PREC_FP64
+    prec = {"fp64": B.GS_PREC_FP64, "fp32": B.GS_PREC_FP32, "bf16": B.GS_PREC_BF16}[args.precision]
     variant = {"row": B.GS_SPMV_ROW, "srbk": B.GS_SPMV_SRBK, "ff": B.GS_SPMV_ROW_FF}[args.spmv]
     mp, ndom = B.gs_partition(systems[0].X, N)  # once per mesh, before timing
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
@@ -787,8 +788,11 @@ def main():
                     B.gs_mat_destroy(mat)
                 return [int(v) for v in it], [float(v) for v in rel], outer
 
-            for s in dsys:  # warm-up, one solve per system
+            mixed_one(dsys[0])  # warm-up
+            B.gs_profile_begin(ctx, range(B.GS_K_COUNT))  # per-class times of one step, outside the timed region
+            for s in dsys:
                 mixed_one(s)
+            m_launch, m_ms = B.gs_profile_end(ctx)
             barrier()
             torch.cuda.synchronize()
             g0 = torch.cuda.Event(enable_timing=True)
@@ -812,6 +816,8 @@ def main():
                 "true_rel_residual_last_system": ((b - Ax).norm(dim=1) / b.norm(dim=1)).tolist(),
                 # both solves stop on the 1e-6 residual test; their distance (last system)
                 "rel_error_vs_fp64_max": float(((x - x_fp64).norm(dim=1) / x_fp64.norm(dim=1)).max()),
+                "phase_ms_one_step": {B.K_NAMES[k]: round(float(m_ms[k]), 2) for k in range(B.GS_K_COUNT)},
+                "launches_one_step": {B.K_NAMES[k]: int(m_launch[k]) for k in range(B.GS_K_COUNT)},
             }
 
         for name, vprec, inner32 in variants:
@@ -974,7 +980,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == B.GS_PREC_FP64 else "f64+f32-precond",
+        "dtype": "f64" if prec == B.GS_PREC_FP64 else f"f64+{args.precision}-precond",
         "data": "synthetic",
         "config": {
             "workload": f"tet cube {args.grid}^3 stiffness sweep E=1e5,1e7,1e9; {len(systems[0].contacts)} contacts; "

@@ -155,6 +155,8 @@ int level0_bf16_launch(gs_ctx ctx, gs_mas mas, bool f32_node_major, int nrhs, co
 // Level-0 product of the FP64 form on the BF16 tensor cores by exact digit
 // splitting (FP64 accuracy); mas_apply_f64tc.cu.
 bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs);
+// FP32 level-0 product from a bulk-copied inverse (mas_apply.cu)
+bool level0_f32_bulk_usable(gs_mas mas, int nrhs);
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas);
 // skip (device, may be null): the kernels return at once while *skip is set
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
@@ -214,6 +216,8 @@ struct gs_mas_s {
   int32_t* remap0 = nullptr;       // device int32[n_items[0]], slot -> node or -1
   std::vector<double*> inv64;      // per level: n_domains * (3N)^2
   std::vector<float*> inv32;       // per level (FP32 precision, or made for the mixed solve)
+  float* inv32p = nullptr;         // FP32 precision, level 0: each domain's inverse as its lower triangle
+                                   // packed by rows (ld(ld+1)/2 floats, padded to a multiple of 4)
   std::vector<void*> inv16;        // BF16 precision: level 0 only, inverse Cholesky factor W, row-major
   void* inv16_tc = nullptr;        // BF16 precision: level-0 W in the tensor-core operand layout
   std::vector<void*> dig64;        // FP64 precision: per level, the inverses as 7 BF16 digit matrices per domain

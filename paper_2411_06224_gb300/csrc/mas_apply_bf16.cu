@@ -19,7 +19,10 @@
 //     again into hi + lo and writes the B operand of MMA 2;
 //   * MMA 2: z = W^T [y_hi | y_lo] with the same shared-memory copy of W read
 //     as an MN-major operand (the transposed A), TMEM columns 16..31;
-//   * epilogue: z = hi + lo columns, plus the prolongated coarse results.
+//   * epilogue: z = hi + lo columns, plus the prolongated coarse results,
+//     summed in FP32 (every level's product is FP32) with the FP64 <-> FP32
+//     conversions done on bit patterns: on this part conversion
+//     instructions run on the FP64 pipe, which otherwise bounds the kernel.
 // All waits are bounded; on a timeout the kernel sets kErrTimeout, skips the
 // rest and still frees its TMEM.
 //
@@ -28,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "primitives.cuh"
 #include "umma.cuh"
 
 namespace gs {
@@ -66,7 +70,7 @@ __device__ __forceinline__ void put_hi_lo(unsigned char* sB, int kk, int k, floa
 template <bool kF32>
 __device__ __forceinline__ float load_r(const void* rv, int64_t stride, int nrhs, int32_t node, int k, int c) {
   if (kF32) return ((const float*)rv)[((int64_t)node * nrhs + k) * 3 + c];
-  return (float)((const double*)rv)[k * stride + 3 * (int64_t)node + c];
+  return f64_to_f32_bits(((const double*)rv)[k * stride + 3 * (int64_t)node + c]);
 }
 
 // z at (node, c) for RHS 0..nrhs-1: level-0 value plus the coarse levels.
@@ -85,12 +89,12 @@ __device__ __forceinline__ void store_z(const Levels& al, const void* zlv, int64
       for (int l = 1; l < 8; ++l)
         if (l < al.L) w += ((const float*)zlv)[(citem[l] * nrhs + k) * 3 + c];
       ((float*)zv)[((int64_t)node * nrhs + k) * 3 + c] = w;
-    } else {
-      double w = (double)v[k];
+    } else {  // the sum in FP32, the precision of every level's product; conversions from bit patterns
+      float w = v[k];
 #pragma unroll
       for (int l = 1; l < 8; ++l)
-        if (l < al.L) w += ((const double*)zlv)[k * lstride + 3 * citem[l] + c];
-      ((double*)zv)[k * stride + 3 * (int64_t)node + c] = w;
+        if (l < al.L) w += f64_to_f32_bits(((const double*)zlv)[k * lstride + 3 * citem[l] + c]);
+      ((double*)zv)[k * stride + 3 * (int64_t)node + c] = f32_to_f64_bits(w);
     }
   }
 }
@@ -291,10 +295,10 @@ __global__ void __launch_bounds__(768) k_level0_cores(const __nv_bfloat16* __res
         w += ((const float*)zlv)[((al.vec_off[l] + al.coarse[l][node]) * nrhs + k) * 3 + c];
       ((float*)zv)[((int64_t)node * nrhs + k) * 3 + c] = w;
     } else {
-      double w = (double)acc[q];
+      float w = acc[q];
       for (int l = 1; l < al.L; ++l)
-        w += ((const double*)zlv)[k * lstride + 3 * (al.vec_off[l] + al.coarse[l][node]) + c];
-      ((double*)zv)[k * stride + 3 * (int64_t)node + c] = w;
+        w += f64_to_f32_bits(((const double*)zlv)[k * lstride + 3 * (al.vec_off[l] + al.coarse[l][node]) + c]);
+      ((double*)zv)[k * stride + 3 * (int64_t)node + c] = f32_to_f64_bits(w);
     }
   }
 }

@@ -19,9 +19,10 @@
 // call may follow a cudaDeviceReset in the same process.  All calls share the
 // array: the restricted vectors are cleared at the start of every call, and
 // two calls whose work overlaps on the GPU (different streams, or different
-// threads on one device) race on it.  Where the level-0 product runs on the
-// tensor cores, the call waits for its stream and returns the status of that
-// product's bounded waits, like gs_mas_apply.
+// threads on one device) race on it.  Where the level-0 product waits on an
+// asynchronous copy (tensor-core and bulk-copy kernels), the call waits for
+// its stream and returns the status of those bounded waits, like
+// gs_mas_apply.
 // With the profiler switched on (gs_profile_begin) the library may create
 // CUDA events; it is off unless the caller turns it on.
 #include <mutex>
@@ -81,7 +82,8 @@ extern "C" int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, dou
   double* base = nullptr;
   GS_TRY(gs::scratch_address(ctx->device, &base));
   GS_TRY(gs::mas_apply_launch(ctx, mas, r, z, nrhs, base, base + per));
-  if (gs::level0_bf16_on_tensor_cores(ctx, mas, nrhs) || gs::level0_f64tc_usable(ctx, mas, nrhs)) {
+  if (gs::level0_bf16_on_tensor_cores(ctx, mas, nrhs) || gs::level0_f64tc_usable(ctx, mas, nrhs) ||
+      gs::level0_f32_bulk_usable(mas, nrhs)) {
     // The tensor-core kernels end a wait that runs past its limit with a bit
     // in the context's device error word.  Read and clear it here (a copy
     // into the context's pinned word, no allocation), so that this call

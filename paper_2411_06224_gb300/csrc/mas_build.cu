@@ -398,6 +398,25 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
   if (i < n) b[i] = (float)a[i];
 }
 
+// Level-0 inverses (FP64, full, symmetric) -> FP32 lower triangles packed by
+// rows, rounded to nearest as k_to_float rounds them; `pitch` floats per domain.
+__global__ void k_pack_lower_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n_dom, int ld,
+                                 int pitch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_dom * pitch) return;
+  const int64_t d = t / pitch;
+  const int p = (int)(t - d * pitch);
+  if (p >= ld * (ld + 1) / 2) {
+    b[t] = 0.0f;
+    return;
+  }
+  int i = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);  // row of packed index p
+  while (i * (i + 1) / 2 > p) --i;
+  while ((i + 1) * (i + 2) / 2 <= p) ++i;
+  const int j = p - i * (i + 1) / 2;
+  b[t] = (float)a[d * ld * ld + (int64_t)i * ld + j];
+}
+
 // double -> float -> bfloat16, both roundings to nearest even
 __global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -417,6 +436,7 @@ int gs_mas_destroy(gs_mas mas) {
   for (auto p : mas->up) c->release(p);
   for (auto p : mas->inv64) c->release(p);
   for (auto p : mas->inv32) c->release(p);
+  c->release(mas->inv32p);
   for (auto p : mas->inv16) c->release(p);
   c->release(mas->inv16_tc);
   for (auto p : mas->dig64) c->release(p);
@@ -609,6 +629,12 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
       if ((s = ctx->alloc((void**)&f, (size_t)cnt * 4))) return fail(s);
       mas->inv32[l] = f;
       { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt); }
+    }
+    if (opts->precision == GS_PREC_FP32) {  // level 0 also as packed lower triangles (the streamed apply)
+      const int pitch = ((ld * (ld + 1) / 2 + 3) / 4) * 4;
+      const int64_t cnt = (int64_t)mas->n_domains[0] * pitch;
+      if ((s = ctx->alloc((void**)&mas->inv32p, (size_t)cnt * 4))) return fail(s);
+      { GS_PROF(ctx, GS_K_MAS_INVERT); k_pack_lower_f32<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[0], mas->inv32p, mas->n_domains[0], ld, pitch); }
     }
   }
   // multilevel vector layout for the apply (levels >= 1, padded per domain)

@@ -34,6 +34,30 @@ __device__ __forceinline__ void head_segmented_reduce(double (&v)[K], int lane, 
   }
 }
 
+// Conversions between FP64 and FP32 from the bit patterns.  On this part the
+// conversion instructions run on the FP64 pipe (2 per clock per SM); these use
+// integer instructions only.
+// double -> float rounded to nearest (ties away from zero); a value below the
+// float normal range becomes a signed zero, one above it infinity.
+__device__ __forceinline__ float f64_to_f32_bits(double v) {
+  const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+  const unsigned sign = hw & 0x80000000u;
+  const int ef = (int)((hw >> 20) & 0x7ffu);
+  const int fe = ef - 896;  // float exponent field (biases 1023 and 127)
+  if (ef == 0 || fe <= 0) return __uint_as_float(sign);
+  if (ef == 0x7ff || fe >= 255) return __uint_as_float(sign | 0x7f800000u | (ef == 0x7ff && ((hw & 0xfffffu) | lw) ? 0x400000u : 0u));
+  const unsigned bits = sign | ((unsigned)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+  return __uint_as_float(bits + ((lw >> 28) & 1u));  // a carry into the exponent rounds up exactly
+}
+// float -> double, exact; a subnormal float (below 2^-126) becomes a signed zero.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned fe = (b >> 23) & 0xffu;
+  if (fe == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+  const unsigned de = fe == 0xffu ? 0x7ffu : fe + 896u;
+  return __hiloint2double((int)((b & 0x80000000u) | (de << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+
 // Stored inverse entry -> arithmetic type (FP64, FP32 or BF16 storage).
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ float widen(float v) { return v; }
