@@ -244,6 +244,89 @@ def test_partition_boxes_are_connected_on_tet_cube():
     assert max(ncomp) == 1
 
 
+def _csr_from_edges(V, edges):
+    nb = [[] for _ in range(V)]
+    for a, b in edges:
+        nb[a].append(b), nb[b].append(a)
+    ptr = np.cumsum([0] + [len(x) for x in nb])
+    adj = np.array([v for x in nb for v in sorted(x)], dtype=np.int64)
+    return ptr, adj
+
+
+def test_components_by_brute_force_search():
+    # numbered by their smallest vertex: {0, 4, 7}, {1, 2}, {3}, {5, 6, 8}
+    edges = [(0, 4), (4, 7), (2, 1), (5, 8), (8, 6)]
+    ptr, adj = _csr_from_edges(9, edges)
+    assert list(partition.components(9, ptr, adj)) == [0, 1, 1, 2, 0, 3, 3, 0, 3]
+    # random graphs: same components as a depth-first search from each unseen vertex
+    rng = np.random.default_rng(0)
+    for V in (1, 17, 60):
+        edges = [tuple(e) for e in rng.integers(0, V, (V // 2, 2)) if e[0] != e[1]]
+        ptr, adj = _csr_from_edges(V, edges)
+        comp = -np.ones(V, dtype=int)
+        c = 0
+        for s0 in range(V):
+            if comp[s0] >= 0:
+                continue
+            stack = [s0]
+            comp[s0] = c
+            while stack:
+                u = stack.pop()
+                for w in adj[ptr[u]:ptr[u + 1]]:
+                    if comp[w] < 0:
+                        comp[w] = c
+                        stack.append(w)
+            c += 1
+        assert np.array_equal(partition.components(V, ptr, adj), comp)
+
+
+def test_component_bisection_never_mixes_bodies():
+    # two interleaved combs of points on a line: plain bisection mixes them,
+    # the component rule bisects each comb on its own, parts numbered comb by comb
+    V, N = 40, 4
+    X = np.stack([np.arange(V, dtype=float), np.zeros(V), np.zeros(V)], 1)
+    edges = [(i, i + 2) for i in range(V - 2)]  # evens and odds: two chains
+    ptr, adj = _csr_from_edges(V, edges)
+    plain = partition.recursive_bisection(X, N)
+    assert any(len(set(np.arange(V)[plain == q] % 2)) > 1 for q in range(plain.max() + 1))
+    part = partition.component_bisection(X, N, ptr, adj)
+    for q in range(part.max() + 1):
+        assert len(set(np.arange(V)[part == q] % 2)) == 1
+    # each comb's parts are the plain bisection of that comb alone, shifted
+    evens, odds = np.arange(0, V, 2), np.arange(1, V, 2)
+    pe = partition.recursive_bisection(X[evens], N)
+    po = partition.recursive_bisection(X[odds], N)
+    assert np.array_equal(part[evens], pe) and np.array_equal(part[odds], po + pe.max() + 1)
+    # a connected mesh: the same as plain bisection
+    s = make_tet_system(6, n_contacts=0, seed=2)
+    assert np.array_equal(partition.component_bisection(s.X, 16, s.adj_ptr, s.adj),
+                          partition.recursive_bisection(s.X, 16))
+
+
+def test_morton_codes_hand_worked():
+    # 2 bits per axis over the unit box: q = min(floor(4 x), 3); bit b of axis a
+    # goes to position 3b + a
+    X = np.array([[0, 0, 0], [1, 1, 1], [0.5, 0, 0], [0, 0.5, 0], [0, 0, 0.75], [0.25, 0.3, 0.1]], dtype=float)
+    X = np.vstack([X, [[1.0, 1.0, 1.0]]])
+    codes = partition.morton_codes(X, bits=2)
+    assert list(codes[:6]) == [0, 63, 8, 16, 2 ** 2 + 2 ** 5, 1 + 2]
+    # a flat axis quantises to 0
+    Y = np.array([[0.0, 0.0, 5.0], [1.0, 1.0, 5.0]])
+    assert list(partition.morton_codes(Y, bits=1)) == [0, 3]
+
+
+def test_morton_partition_by_sorting():
+    rng = np.random.default_rng(4)
+    X = rng.random((203, 3))
+    X[10] = X[20]  # a tie: broken by vertex index
+    N = 16
+    codes = partition.morton_codes(X)
+    order = sorted(range(203), key=lambda v: (int(codes[v]), v))
+    part = partition.morton_partition(X, N)
+    assert [int(part[v]) for v in order] == [i // N for i in range(203)]
+    assert part[10] == part[20] or order.index(10) // N != order.index(20) // N
+
+
 # ---------------------------------------------------------------- MAS levels (supp. Alg. 2-5)
 
 
