@@ -155,6 +155,31 @@ int gs_partition(int32_t n_nodes, const double* X, int32_t domain_size, int32_t*
 int gs_partition_batch(int32_t n_sys, const int32_t* node_off, const double* X, int32_t domain_size, int32_t* map,
                        int32_t* n_domains);
 
+/* The level-0 partition computed on the device (the paper runs METIS on the
+ * host, Sec. 3.2; these rules are deterministic and bit for bit the host's).
+ * rule GS_PART_RCB: the recursive coordinate bisection of gs_partition.
+ * GS_PART_RCB_COMPONENTS: the same bisection inside each connected component
+ *   of the mesh graph (components numbered by their smallest node), so no
+ *   part mixes two bodies; needs adj_ptr / adj.  On a connected mesh it
+ *   equals GS_PART_RCB.
+ * GS_PART_MORTON: N consecutive nodes in Morton order (each coordinate cut
+ *   to 10 bits over the bounding box, q = min(floor((x - lo) / (hi - lo)
+ *   * 1024), 1023), 0 on a flat axis; bits interleaved x, y, z from the
+ *   lowest; ties by node index): the level-0 subdomains of the earlier MAS
+ *   the paper compares against (Sec. 3.1), for comparisons.
+ * Slots as gs_partition: map[v] = N * part + rank of v among its part's
+ * nodes in ascending index.
+ * X: device double[n * 3]; adj_ptr, adj: device int32 CSR of the mesh graph
+ * (may be NULL except for GS_PART_RCB_COMPONENTS); map: device int32[n];
+ * n_domains: host, receives the part count.  Uses the context's stream and
+ * allocates working memory from its pool.  Errors: GS_ERR_INVALID (a
+ * non-finite position, a neighbour out of range, bad arguments). */
+#define GS_PART_RCB 0
+#define GS_PART_RCB_COMPONENTS 1
+#define GS_PART_MORTON 2
+int gs_partition_device(gs_ctx ctx, int32_t n, const double* X, const int32_t* adj_ptr, const int32_t* adj,
+                        int32_t domain_size, int32_t rule, int32_t* map, int32_t* n_domains);
+
 /* ---------------------------------------------------------------- MAS */
 #define GS_PREC_FP64 0 /* domain inverses stored and applied in FP64 */
 #define GS_PREC_FP32 1 /* inverses rounded to FP32, applied with FP32 accumulation */
@@ -189,6 +214,13 @@ typedef struct gs_mas_opts {
 int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_domains0,
                  const int32_t* adj_ptr, const int32_t* adj, const int32_t* contacts,
                  int64_t n_contacts, const gs_mas_opts* opts, gs_mas* out);
+/* The same build from the mesh itself: the level-0 partition of the node
+ * positions X (device double[n * 3]) by `part_rule` (GS_PART_*) on the
+ * device (gs_partition_device), then gs_build_mas.  The call the paper's
+ * build_mas(BSR, mesh connectivity) names. */
+int gs_build_mas_mesh(gs_ctx ctx, gs_mat mat, const double* X, int32_t part_rule, const int32_t* adj_ptr,
+                      const int32_t* adj, const int32_t* contacts, int64_t n_contacts, const gs_mas_opts* opts,
+                      gs_mas* out);
 
 /* Level count and item counts: n_items[l] for l < *n_levels (n_items may be
  * NULL; it must hold max_levels entries).  Level 0 counts padded slots. */

@@ -26,6 +26,9 @@ GS_ERR_TIMEOUT = -7
 GS_SPMV_SRBK = 0
 GS_SPMV_ROW = 1
 GS_SPMV_ROW_FF = 2
+GS_PART_RCB = 0
+GS_PART_RCB_COMPONENTS = 1
+GS_PART_MORTON = 2
 GS_PREC_FP64 = 0
 GS_PREC_FP32 = 1
 GS_PREC_BF16 = 2
@@ -72,6 +75,8 @@ EXPORTS = [
     "gs_partition",
     "gs_partition_batch",
     "gs_build_mas",
+    "gs_partition_device",
+    "gs_build_mas_mesh",
     "gs_mas_info",
     "gs_mas_export_coarse",
     "gs_mas_export_inverse",
@@ -137,6 +142,11 @@ def lib():
             "gs_spmv": (ctypes.c_int, [_P, _P, _P, _P, _I32, _I32]),
             "gs_partition": (ctypes.c_int, [_I32, _P, _I32, _P, ctypes.POINTER(_I32)]),
             "gs_partition_batch": (ctypes.c_int, [_I32, _P, _P, _I32, _P, ctypes.POINTER(_I32)]),
+            "gs_partition_device": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I32, _I32, _P, ctypes.POINTER(_I32)]),
+            "gs_build_mas_mesh": (
+                ctypes.c_int,
+                [_P, _P, _P, _I32, _P, _P, _P, _I64, ctypes.POINTER(gs_mas_opts), ctypes.POINTER(_P)],
+            ),
             "gs_build_mas": (
                 ctypes.c_int,
                 [_P, _P, _P, _I32, _P, _P, _P, _I64, ctypes.POINTER(gs_mas_opts), ctypes.POINTER(_P)],
@@ -301,6 +311,38 @@ def gs_partition_batch(X, node_off, domain_size):
         "gs_partition_batch",
     )
     return mp, nd.value
+
+
+def gs_partition_device(ctx, X, domain_size, rule=GS_PART_RCB, adj_ptr=None, adj=None):
+    """Device partition of positions X ((V, 3) float64 CUDA tensor) -> (map int32 CUDA tensor (V,), n_domains)."""
+    V = X.shape[0]
+    mp = torch.empty(V, dtype=torch.int32, device=X.device)
+    nd = _I32()
+    _check(
+        lib().gs_partition_device(ctx, V, _dev(X, torch.float64, "X"),
+                                  _dev(adj_ptr, torch.int32, "adj_ptr") if adj_ptr is not None else None,
+                                  _dev(adj, torch.int32, "adj") if adj is not None else None, domain_size, rule,
+                                  _dev(mp, torch.int32, "map"), ctypes.byref(nd)),
+        "gs_partition_device",
+    )
+    return mp, nd.value
+
+
+def gs_build_mas_mesh(ctx, mat, X, adj_ptr, adj, contacts, domain_size=32, max_levels=2, precision=GS_PREC_FP64,
+                      part_rule=GS_PART_RCB):
+    """The MAS with its level-0 partition computed on the device from X ((V, 3) float64 CUDA tensor)."""
+    h = _P()
+    opts = gs_mas_opts(domain_size, max_levels, precision)
+    P = 0 if contacts is None else contacts.shape[0]
+    _check(
+        lib().gs_build_mas_mesh(
+            ctx, mat, _dev(X, torch.float64, "X"), part_rule, _dev(adj_ptr, torch.int32, "adj_ptr"),
+            _dev(adj, torch.int32, "adj"), _dev(contacts, torch.int32, "contacts") if P else None, P,
+            ctypes.byref(opts), ctypes.byref(h),
+        ),
+        "gs_build_mas_mesh",
+    )
+    return h
 
 
 def gs_build_mas(ctx, mat, map_, n_domains0, adj_ptr, adj, contacts, domain_size=32, max_levels=2,

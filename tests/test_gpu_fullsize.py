@@ -62,6 +62,9 @@ def test_full_assembly_and_partition(B, full):
     assert np.all(np.abs(au.cpu().numpy() - full["au"]) <= 1e-13 * abs_sum)
     mo, _ = partition.map_remap(partition.recursive_bisection(s.X, N), N)
     assert np.array_equal(full["mp"], mo)
+    # the device partition, bit for bit
+    md, ndd = B.gs_partition_device(full["ctx"], dev(s.X, torch.float64), N, B.GS_PART_RCB)
+    assert ndd == full["nd"] and np.array_equal(md.cpu().numpy(), mo)
 
 
 def test_full_levels_spmv_apply(B, full):
