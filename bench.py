@@ -73,6 +73,8 @@ def parse():
                    help="force a launch shape after tuning (names as in config.launch_shapes), e.g. "
                         "spmv_lanes=2; repeatable")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--partition-steps", type=int, default=1,
+                   help="timed solves per variant of the partition / level comparison (0 = skip)")
     p.add_argument("--no-config1", dest="config1", action="store_false",
                    help="skip the plain FP64 solve of the 16^3 cube (forms.plain16)")
     p.add_argument("--micro", action="store_true",
@@ -952,6 +954,69 @@ def main():
             "graph": "whole PCG loop = one CUDA graph launch (conditional WHILE node)",
         }
 
+    # level-0 partitions and level counts compared (the paper's Table MAS:
+    # connectivity-enhanced MAS against the Morton-order MAS of Wu et al.,
+    # and block-Jacobi), on the stiffest sweep system and on a scene of
+    # separate bodies interleaved in one box; the partition runs on the
+    # device inside the timed build
+    partitions = None
+    if args.partition_steps > 0:
+        from synth.workloads import uneven_batch
+
+        def compare(rows_, cols_, blocks_, Vn, Xd, ptr_d, adj_d, con_d, bb, nr, variants):
+            out = {}
+            for name, rule, levels in variants:
+                xx = torch.zeros_like(bb)
+
+                def run():
+                    b0 = torch.cuda.Event(enable_timing=True)
+                    b1 = torch.cuda.Event(enable_timing=True)
+                    b2 = torch.cuda.Event(enable_timing=True)
+                    b0.record(stream)
+                    mat = B.gs_assemble(ctx, Vn, rows_, cols_, blocks_)
+                    mas = B.gs_build_mas_mesh(ctx, mat, Xd, ptr_d, adj_d, con_d, domain_size=N, max_levels=levels,
+                                              part_rule=rule)
+                    b1.record(stream)
+                    it, _, _ = B.gs_pcg_solve(ctx, mat, mas, bb, xx, nrhs=nr, tol=TOL, max_iter=20000,
+                                              variant=variant)
+                    b2.record(stream)
+                    torch.cuda.synchronize()
+                    nl = B.gs_mas_info(mas)
+                    B.gs_mas_destroy(mas)
+                    B.gs_mat_destroy(mat)
+                    return it, b0.elapsed_time(b1), b1.elapsed_time(b2), nl
+
+                run()  # warm-up
+                it, t_build, t_pcg = None, 0.0, 0.0
+                for _ in range(args.partition_steps):
+                    it, tb, tp, nl = run()
+                    t_build += tb / args.partition_steps
+                    t_pcg += tp / args.partition_steps
+                out[name] = {"pcg_iterations": [int(v) for v in it], "levels": nl[1],
+                             "ms_assembly_and_build": t_build, "ms_pcg": t_pcg,
+                             "solves_per_s": 1e3 / (t_build + t_pcg)}
+            return out
+
+        variants = [("ce_mas_rcb", B.GS_PART_RCB, L), ("mas_morton", B.GS_PART_MORTON, L),
+                    ("block_jacobi", B.GS_PART_RCB, 1)]
+        sx = systems[-1]
+        Xs = t(sx.X, torch.float64)
+        partitions = {"sweep_E1e9": {
+            "workload": f"{args.grid}^3 sweep system E=1e9, {args.nrhs} RHS, N=32, tol 1e-6",
+            **compare(dsys[-1]["rows"], dsys[-1]["cols"], dsys[-1]["blocks"], V, Xs, shared["adj_ptr"],
+                      shared["adj"], shared["contacts"], b, args.nrhs, variants)}}
+        bt = uneven_batch(24, seed=1006 + rank)
+        Vb = bt.n_vertices
+        rb = t(np.random.default_rng(3100).normal(size=(1, 3 * Vb)), torch.float64)
+        partitions["interleaved_bodies"] = {
+            "workload": f"24 tet cubes (1k-50k vertices, {Vb} total, E 1e5-1e9) in the same unit box as one "
+                        "system, 1 RHS, N=32, tol 1e-6",
+            **compare(t(bt.rows, torch.int32), t(bt.cols, torch.int32), t(bt.blocks.reshape(-1, 3, 3), torch.float64),
+                      Vb, t(bt.X, torch.float64), t(bt.adj_ptr, torch.int32), t(bt.adj, torch.int32),
+                      t(bt.contacts, torch.int32), rb, 1,
+                      [("ce_mas_rcb_components", B.GS_PART_RCB_COMPONENTS, L), ("ce_mas_rcb", B.GS_PART_RCB, L),
+                       ("mas_morton", B.GS_PART_MORTON, L), ("block_jacobi", B.GS_PART_RCB_COMPONENTS, 1)])}
+
     # the plain FP64 solve on the 16^3 cube
     plain16 = None
     if args.config1:
@@ -1003,7 +1068,8 @@ def main():
         "phase_ms_one_step": {B.K_NAMES[k]: float(ms_1[k]) for k in range(B.GS_K_COUNT)},
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
-        "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth, "plain16": plain16},
+        "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth, "plain16": plain16,
+                  "partitions": partitions},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),
