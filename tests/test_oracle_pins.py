@@ -664,3 +664,90 @@ def test_inverse_factors_reproduce_the_inverses():
                 continue
             WMW = fac[d] @ mats[l][d] @ fac[d].T
             np.testing.assert_allclose(WMW[np.ix_(real, real)], np.eye(real.sum()), atol=1e-9)
+
+
+# ---------------------------------------------------------------- element Hessians (Sec. 3.1)
+from oracle import elastic  # noqa: E402
+
+
+def _deformed_tets(seed=0, T=5):
+    rng = np.random.default_rng(seed)
+    X = rng.random((4 * T, 3))
+    tets = np.arange(4 * T).reshape(T, 4)
+    # keep positive orientation
+    for t in range(T):
+        a, b, c, d = X[tets[t]]
+        if np.linalg.det(np.stack([b - a, c - a, d - a], 1)) < 0:
+            tets[t, [1, 2]] = tets[t, [2, 1]]
+    x = X @ (np.eye(3) + 0.3 * rng.normal(size=(3, 3))).T + 0.05 * rng.normal(size=X.shape)
+    return X, x, tets
+
+
+def test_snh_gradient_and_hessian_by_central_differences():
+    X, x, tets = _deformed_tets()
+    E, nu = 1e6, 0.4
+    e0, g = elastic.energy_and_gradient(X, x, tets, E, nu)
+    h = 1e-6
+    gd = np.zeros_like(x)
+    for v in range(x.shape[0]):
+        for i in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, i] += h
+            xm[v, i] -= h
+            gd[v, i] = (elastic.energy_and_gradient(X, xp, tets, E, nu)[0] -
+                        elastic.energy_and_gradient(X, xm, tets, E, nu)[0]) / (2 * h)
+    assert np.abs(gd - g).max() <= 1e-6 * np.abs(g).max()
+    # the unprojected element Hessian is the derivative of the gradient
+    He = elastic.element_hessians(X, x, tets, E, nu, project=False)
+    for t in range(tets.shape[0]):
+        Hd = np.zeros((12, 12))
+        for a in range(4):
+            for i in range(3):
+                xp, xm = x.copy(), x.copy()
+                xp[tets[t, a], i] += h
+                xm[tets[t, a], i] -= h
+                dg = (elastic.energy_and_gradient(X, xp, tets[t:t + 1], E, nu)[1] -
+                      elastic.energy_and_gradient(X, xm, tets[t:t + 1], E, nu)[1]) / (2 * h)
+                Hd[:, 3 * a + i] = dg[tets[t]].reshape(-1)
+        assert np.abs(Hd - He[t]).max() <= 1e-5 * np.abs(He[t]).max()
+
+
+def test_snh_rest_state_rotation_invariance_and_projection():
+    mu, lam = elastic.lame(1e6, 0.4)
+    _, g, _ = elastic.snh(np.eye(3), mu, lam)
+    assert np.abs(g).max() <= 1e-9 * mu  # the rest state is stationary
+    rng = np.random.default_rng(1)
+    F = np.eye(3) + 0.4 * rng.normal(size=(3, 3))
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    Q *= np.sign(np.linalg.det(Q))
+    assert abs(elastic.snh(Q @ F, mu, lam)[0] - elastic.snh(F, mu, lam)[0]) <= 1e-9 * mu
+    # projection: PSD output, identity on PSD input
+    _, _, H = elastic.snh(np.diag([1.8, 0.3, 0.4]), mu, lam)
+    assert np.linalg.eigvalsh(H).min() < 0  # a compressed state with a negative mode
+    P = elastic.psd_project(H)
+    assert np.linalg.eigvalsh(P).min() >= -1e-9 * np.abs(H).max()
+    S = H @ H.T
+    np.testing.assert_allclose(elastic.psd_project(S), S, rtol=0, atol=1e-9 * np.abs(S).max())
+
+
+def test_system_triplets_assemble_the_scattered_element_hessians():
+    from synth.mesh import tet_cube
+
+    rng = np.random.default_rng(2)
+    X, tets = tet_cube(3, rng)
+    x = X + 0.05 * rng.normal(size=X.shape)
+    E, nu, rho, dt = 1e5, 0.4, 1000.0, 0.01
+    rows, cols, blocks = elastic.system_triplets(X, x, tets, E, nu, rho, dt)
+    assert np.all(rows <= cols)
+    rid, cid, au = assembly.assemble(rows, cols, blocks)
+    V = X.shape[0]
+    A = assembly.to_dense(V, rid, cid, au)
+    # brute force: every element's 12 x 12 Hessian added at its nodes, plus the masses
+    He = elastic.element_hessians(X, x, tets, E, nu)
+    D = np.zeros_like(A)
+    for t, tet in enumerate(tets):
+        idx = (3 * np.asarray(tet)[:, None] + np.arange(3)).ravel()
+        D[np.ix_(idx, idx)] += He[t]
+    D += np.kron(np.diag(elastic.lumped_mass(X, tets, rho) / dt ** 2), np.eye(3))
+    np.testing.assert_allclose(A, D, rtol=0, atol=1e-10 * np.abs(D).max())
+    assert np.linalg.eigvalsh(A).min() > 0
