@@ -751,3 +751,82 @@ def test_system_triplets_assemble_the_scattered_element_hessians():
     D += np.kron(np.diag(elastic.lumped_mass(X, tets, rho) / dt ** 2), np.eye(3))
     np.testing.assert_allclose(A, D, rtol=0, atol=1e-10 * np.abs(D).max())
     assert np.linalg.eigvalsh(A).min() > 0
+
+
+# ---------------------------------------------------------------- Newton loop on the incremental potential
+def _newton_case(n=3, seed=5, n_springs=6):
+    from synth.mesh import tet_cube
+
+    rng = np.random.default_rng(seed)
+    X, tets = tet_cube(n, rng)
+    V = X.shape[0]
+    xt = X + 0.02 * rng.normal(size=X.shape)  # predicted positions
+    pairs = rng.choice(V, size=(n_springs, 2), replace=False) if n_springs else np.zeros((0, 2), np.int64)
+    nrm = rng.normal(size=(n_springs, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    K = 1e3 * nrm[:, :, None] * nrm[:, None, :]
+    rest = 0.9 * (X[pairs[:, 0]] - X[pairs[:, 1]]) if n_springs else np.zeros((0, 3))
+    return X, tets, xt, (pairs, K, rest)
+
+
+def test_incremental_potential_gradient_by_central_differences():
+    from oracle import newton
+
+    X, tets, xt, springs = _newton_case()
+    rng = np.random.default_rng(1)
+    x = X + 0.05 * rng.normal(size=X.shape)
+    args = (tets, 1e4, 0.3, 1000.0, 0.01, xt, springs)
+    _, g = newton.incremental_potential(X, x, *args)
+    h = 1e-6
+    for _ in range(12):
+        v, c = rng.integers(X.shape[0]), rng.integers(3)
+        xp, xm = x.copy(), x.copy()
+        xp[v, c] += h
+        xm[v, c] -= h
+        fd = (newton.incremental_potential(X, xp, *args)[0] - newton.incremental_potential(X, xm, *args)[0]) / (2 * h)
+        assert abs(fd - g[v, c]) <= 1e-6 * max(1.0, abs(g).max())
+
+
+def test_spring_hessian_is_the_exact_derivative_of_the_spring_gradient():
+    from oracle import assembly, newton
+
+    X, _, _, springs = _newton_case(n_springs=8)
+    V = X.shape[0]
+    rng = np.random.default_rng(2)
+    x = X + 0.1 * rng.normal(size=X.shape)
+    _, g0, (r, c, b) = newton.spring_terms(x, springs)
+    A = assembly.to_dense(V, *assembly.assemble(r, c, b))
+    dx = rng.normal(size=X.shape)
+    _, g1, _ = newton.spring_terms(x + dx, springs)
+    # the springs are quadratic: the gradient changes by exactly H dx
+    assert np.allclose((g1 - g0).ravel(), A @ dx.ravel(), rtol=0, atol=1e-9 * abs(A).max())
+
+
+def test_newton_stops_at_once_at_the_rest_state():
+    from oracle import newton
+
+    X, tets, _, (pairs, K, _) = _newton_case()
+    rest = X[pairs[:, 0]] - X[pairs[:, 1]]  # springs at rest too
+    x, hist = newton.newton(X, X, tets, 1e5, 0.4, 1000.0, 0.01, X, (pairs, K, rest))
+    assert len(hist) == 1 and hist[0]["converged"] and hist[0]["dinf"] < 1e-12
+    assert np.array_equal(x, X)
+
+
+def test_newton_reaches_the_minimiser_found_by_a_derivative_free_method():
+    import scipy.optimize as so
+
+    from oracle import newton
+
+    X, tets, xt, springs = _newton_case(n=2, seed=8, n_springs=3)
+    args = (tets, 1e4, 0.3, 1000.0, 0.01, xt, springs)
+    rng = np.random.default_rng(3)
+    x0 = X + 0.03 * rng.normal(size=X.shape)
+    x, hist = newton.newton(X, x0, *args, tol=1e-9)
+    assert hist[-1]["converged"]
+    energies = [h["energy"] for h in hist]
+    assert all(b < a for a, b in zip(energies, energies[1:]))
+    # Powell (no derivatives) on the energy alone, from the same start
+    f = lambda z: newton.incremental_potential(X, z.reshape(-1, 3), *args)[0]
+    res = so.minimize(f, x0.ravel(), method="Powell", options=dict(xtol=1e-12, ftol=1e-15, maxiter=200000))
+    assert np.abs(res.x.reshape(-1, 3) - x).max() <= 1e-5
+    assert f(x.ravel()) <= res.fun + 1e-9 * abs(res.fun)
