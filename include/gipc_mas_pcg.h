@@ -374,6 +374,114 @@ int gs_micro_segment_reduce(gs_ctx ctx, int64_t nb, const uint64_t* keys, const 
 int gs_micro_bsr_spmv_cusparse(gs_ctx ctx, int32_t n, int32_t nnzb, const int32_t* row_ptr, const int32_t* col_ind,
                                const double* vals, const double* x, double* y, int32_t reps, float* ms);
 
+/* ---------------------------------------------------------------- elastic bodies and Newton */
+/* A tet mesh body on the device with the stable Neo-Hookean energy
+ * (Sec. 3.1 names the elastic energies the Hessian is assembled from; the
+ * form used is Smith, de Goes and Kim 2018 without the log term):
+ *   Psi(F) = mu/2 (|F|^2 - 3) + lam/2 (det F - alpha)^2, alpha = 1 + mu/lam,
+ * mu = 4/3 mu_L, lam = lam_L + 5/6 mu_L from Young's modulus E and Poisson's
+ * ratio nu.  The incremental potential of one implicit-Euler step is
+ *   E(x) = sum_t vol_t Psi(F_t) + sum_v m_v/(2 dt^2) |x_v - xt_v|^2
+ *        + sum_springs 1/2 (x_i - x_j - r)^T K (x_i - x_j - r),
+ * m_v = rho (sum of the adjacent rest volumes) / 4.  Its Hessian is the
+ * element Hessians, each projected to positive semi-definite by the analytic
+ * eigensystem of the F-Hessian (negative eigenvalues set to 0), plus
+ * M / dt^2 and the spring blocks [K, -K; -K, K].
+ * Assembly follows the paper's hash-key reduction (Sec. 5.1-5.2) with the
+ * pattern fixed: element keys are sorted once when the body is created,
+ * spring keys whenever the springs change, and every later assembly only
+ * writes values and reduces them in the stored order. */
+typedef struct gs_fem_s* gs_fem;
+
+/* X: device double[n_vertices * 3] rest positions (copied); tets: device
+ * int32[n_tets * 4], four distinct vertices each (copied).  rho: density,
+ * dt: time step.  Errors: GS_ERR_INVALID (sizes, E <= 0, nu outside
+ * [0, 0.5), rho or dt <= 0, an index out of range or repeated in a tet),
+ * GS_ERR_NONFINITE (a rest tet of zero volume). */
+int gs_fem_create(gs_ctx ctx, int32_t n_vertices, int64_t n_tets, const double* X, const int32_t* tets,
+                  double E, double nu, double rho, double dt, gs_fem* out);
+/* Replace the body's springs (contact pairs in the synthetic scenes): pairs
+ * device int32[2 n] of distinct vertices, K device double[9 n] symmetric
+ * PSD 3x3 stiffness (row-major), rest device double[3 n] rest offsets
+ * x_i - x_j.  Copied.  Only these keys are sorted; they are merged into the
+ * element pattern.  n = 0 removes them.  Matrices assembled before the call
+ * can no longer be refilled.  Errors: GS_ERR_INVALID. */
+int gs_fem_set_springs(gs_ctx ctx, gs_fem fem, const int32_t* pairs, const double* K, const double* rest,
+                       int64_t n);
+/* Stored blocks of the merged pattern and of the element part alone; the
+ * Lame parameters (mu, lam) used.  Outputs host, each may be NULL. */
+int gs_fem_info(gs_fem fem, int64_t* n_stored, int64_t* n_element_stored, double* lame_mu, double* lame_lambda);
+/* Rest data: w device double[n_tets * 12] (F = sum_a x_a w_a^T, w[t][a][j]),
+ * vol device double[n_tets], mass device double[n_vertices]; each may be NULL. */
+int gs_fem_export_rest(gs_ctx ctx, gs_fem fem, double* w, double* vol, double* mass);
+/* E(x) (host double) and, if grad is not NULL, its gradient (device
+ * double[3 n_vertices]) at x (device double[3 n_vertices]); xt the
+ * predicted positions, same layout.  Sums in a fixed order (bit-reproducible). */
+int gs_fem_energy(gs_ctx ctx, gs_fem fem, const double* x, const double* xt, double* energy, double* grad);
+/* The Hessian as upper triplets: 10 per tet in the pair order (0,0) (0,1)
+ * (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3), each at (min, max) of its
+ * two vertices (transposed when the first is the larger); then one
+ * m_v / dt^2 I per vertex; then 3 per spring: (i, i) K, (j, j) K,
+ * (min, max) -K.  rows, cols device int32, blocks device double[9 each]
+ * (row-major), 10 n_tets + n_vertices + 3 n_springs entries; rows and cols
+ * may be NULL. */
+int gs_fem_triplets(gs_ctx ctx, gs_fem fem, const double* x, int32_t* rows, int32_t* cols, double* blocks);
+/* A new matrix (gs_mat_destroy) holding the Hessian at x in the body's
+ * pattern. */
+int gs_fem_assemble(gs_ctx ctx, gs_fem fem, const double* x, gs_mat* out);
+/* New values at x into a matrix made by gs_fem_assemble of the same body
+ * since its springs last changed (the numeric phase: no sort).
+ * Errors: GS_ERR_INVALID for a matrix of another pattern. */
+int gs_fem_refill(gs_ctx ctx, gs_fem fem, const double* x, gs_mat mat);
+int gs_fem_destroy(gs_fem fem);
+
+/* New level matrices and inverses for `mat` (same nodes) in an existing
+ * preconditioner: the numeric part of gs_build_mas, keeping the partition
+ * and the levels (they depend only on the graph and the contacts).
+ * Errors: as gs_build_mas; GS_ERR_INVALID for a matrix of another size. */
+int gs_mas_refresh(gs_ctx ctx, gs_mas mas, gs_mat mat);
+
+typedef struct gs_newton_opts {
+  double tol;            /* stop when max_i |d_i| <= tol * dt (the step's velocity is small) */
+  int32_t max_newton;    /* steps at most */
+  double pcg_tol;        /* relative residual of each linear solve */
+  int32_t pcg_max_iter;
+  int32_t spmv_variant;  /* GS_SPMV_* */
+  int32_t domain_size;   /* MAS options */
+  int32_t max_levels;
+  int32_t precision;     /* GS_PREC_* */
+  int32_t part_rule;     /* GS_PART_* level-0 partition of the rest positions */
+  double armijo;         /* c in E(x + a d) <= E(x) + c a g.d, 0 <= c < 1 */
+  int32_t max_halvings;  /* line-search halvings per step at most (the last step is taken) */
+} gs_newton_opts;
+
+typedef struct gs_newton_stats {
+  int32_t iterations;      /* steps taken */
+  int32_t pcg_iterations;  /* summed over the solves */
+  int32_t halvings;        /* line-search halvings, summed */
+  int32_t converged;       /* 1 when the last direction met tol */
+  double energy0, energy;  /* E at the start and at the returned x */
+  double step_inf;         /* max |d| of the last direction */
+  double ms[6];            /* CUDA-event time: energy + gradient, Hessian + assembly, MAS build / refresh,
+                              PCG, line search, total */
+} gs_newton_stats;
+
+/* Newton's method on the incremental potential (Fig. framework; supplement
+ * Eq. 1): per step the gradient, the projected Hessian refilled into the
+ * fixed pattern, the MAS built once (partition of the rest positions by
+ * part_rule, adjacency adj_ptr / adj as in gs_build_mas, springs as
+ * contacts) and refreshed after, d = -H^-1 g by MAS-PCG (an unconverged
+ * solve still gives a descent direction and is used), a stop when
+ * max |d| <= tol dt, and backtracking from a = 1 by halving until the
+ * Armijo condition holds.  x: device double[3 n_vertices], the start,
+ * overwritten by the result; xt: predicted positions.  energies: host
+ * double[max_newton + 1] or NULL, E at every iterate.
+ * Returns GS_OK when converged, GS_ERR_MAXITER after max_newton steps
+ * (x holds the last iterate), GS_ERR_NOT_SPD if g.d >= 0, or the status
+ * of a failed assembly, build or solve. */
+int gs_fem_newton(gs_ctx ctx, gs_fem fem, const double* xt, double* x, const int32_t* adj_ptr,
+                  const int32_t* adj, const gs_newton_opts* opts, gs_newton_stats* stats, double* energies);
+
 /* ---------------------------------------------------------------- measurement */
 /* Kernel classes the library counts (and optionally times) per context.
  * The split follows the paper's cost model T = T_ga + T_pa + N_pcg T_pcg
@@ -388,7 +496,8 @@ int gs_micro_bsr_spmv_cusparse(gs_ctx ctx, int32_t n, int32_t nnzb, const int32_
 #define GS_K_MAS_APPLY_COARSE 7 /* restriction and coarse-level dense products */
 #define GS_K_PCG_VECTOR 8       /* dot products and vector updates */
 #define GS_K_OTHER 9            /* validation and setup kernels */
-#define GS_K_COUNT 10
+#define GS_K_ELEMENT 10         /* element Hessians, forces, energies and rest shapes (gs_fem_*) */
+#define GS_K_COUNT 11
 
 /* Start counting kernel launches per class on `ctx`; classes whose bit is
  * set in `timed_classes` are also bracketed by CUDA events on the context

@@ -44,7 +44,8 @@ GS_K_MAS_APPLY_L0 = 6
 GS_K_MAS_APPLY_COARSE = 7
 GS_K_PCG_VECTOR = 8
 GS_K_OTHER = 9
-GS_K_COUNT = 10
+GS_K_ELEMENT = 10
+GS_K_COUNT = 11
 GS_TUNE_SPMV_LANES = 0
 GS_TUNE_SPMV32_LANES = 1
 GS_TUNE_APPLY_RHS = 2
@@ -57,7 +58,7 @@ GS_TUNE_SPMV_FF_RHS = 8
 GS_TUNE_COUNT = 9
 
 K_NAMES = ["assemble", "libprim", "spmv", "mas_levels", "mas_matrices", "mas_invert", "mas_apply_l0",
-           "mas_apply_coarse", "pcg_vector", "other"]
+           "mas_apply_coarse", "pcg_vector", "other", "element"]
 
 # Every symbol the header declares (checked by the test-suite).
 EXPORTS = [
@@ -95,6 +96,17 @@ EXPORTS = [
     "gs_micro_bsr_spmv_cusparse",
     "gs_ctx_alloc_stats",
     "gs_debug_raise_flags",
+    "gs_fem_create",
+    "gs_fem_set_springs",
+    "gs_fem_info",
+    "gs_fem_export_rest",
+    "gs_fem_energy",
+    "gs_fem_triplets",
+    "gs_fem_assemble",
+    "gs_fem_refill",
+    "gs_fem_destroy",
+    "gs_mas_refresh",
+    "gs_fem_newton",
 ]
 
 
@@ -106,6 +118,22 @@ class GsError(RuntimeError):
 
 class gs_mas_opts(ctypes.Structure):
     _fields_ = [("domain_size", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class gs_newton_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
+                ("pcg_max_iter", ctypes.c_int32), ("spmv_variant", ctypes.c_int32), ("domain_size", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32), ("part_rule", ctypes.c_int32),
+                ("armijo", ctypes.c_double), ("max_halvings", ctypes.c_int32)]
+
+
+class gs_newton_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("pcg_iterations", ctypes.c_int32), ("halvings", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("energy0", ctypes.c_double), ("energy", ctypes.c_double),
+                ("step_inf", ctypes.c_double), ("ms", ctypes.c_double * 6)]
+
+
+NEWTON_PHASES = ["energy_gradient", "hessian_assembly", "mas", "pcg", "line_search", "total"]
 
 
 _lib = None
@@ -171,6 +199,19 @@ def lib():
             "gs_profile_end": (ctypes.c_int, [_P, _P, _P]),
             "gs_ctx_alloc_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
             "gs_debug_raise_flags": (ctypes.c_int, [_P, _I32]),
+            "gs_fem_create": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _D, _D, _D, _D, ctypes.POINTER(_P)]),
+            "gs_fem_set_springs": (ctypes.c_int, [_P, _P, _P, _P, _P, _I64]),
+            "gs_fem_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_D),
+                                           ctypes.POINTER(_D)]),
+            "gs_fem_export_rest": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+            "gs_fem_energy": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
+            "gs_fem_triplets": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+            "gs_fem_assemble": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
+            "gs_fem_refill": (ctypes.c_int, [_P, _P, _P, _P]),
+            "gs_fem_destroy": (ctypes.c_int, [_P]),
+            "gs_mas_refresh": (ctypes.c_int, [_P, _P, _P]),
+            "gs_fem_newton": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(gs_newton_opts),
+                                             ctypes.POINTER(gs_newton_stats), _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -511,3 +552,94 @@ def gs_micro_bsr_spmv_cusparse(ctx, n, row_ptr, col_ind, vals, x, y, reps=10):
                                             ctypes.byref(ms)),
            "gs_micro_bsr_spmv_cusparse")
     return ms.value
+
+
+# ---------------------------------------------------------------- elastic bodies and Newton
+def gs_fem_create(ctx, X, tets, E, nu, rho, dt):
+    """X: (V, 3) float64, tets: (T, 4) int32 CUDA tensors (copied)."""
+    h = _P()
+    _check(lib().gs_fem_create(ctx, X.shape[0], tets.shape[0], _dev(X, torch.float64, "X"),
+                               _dev(tets, torch.int32, "tets"), E, nu, rho, dt, ctypes.byref(h)), "gs_fem_create")
+    return h
+
+
+def gs_fem_set_springs(ctx, fem, pairs, K, rest):
+    """pairs (P, 2) int32, K (P, 3, 3) float64, rest (P, 3) float64 CUDA tensors; P = 0 or None removes them."""
+    n = 0 if pairs is None else pairs.shape[0]
+    _check(lib().gs_fem_set_springs(ctx, fem, _dev(pairs, torch.int32, "pairs") if n else None,
+                                    _dev(K, torch.float64, "K") if n else None,
+                                    _dev(rest, torch.float64, "rest") if n else None, n), "gs_fem_set_springs")
+
+
+def gs_fem_info(fem):
+    """(stored blocks, element-only stored blocks, mu, lam)."""
+    u, ue, mu, lam = _I64(), _I64(), _D(), _D()
+    _check(lib().gs_fem_info(fem, ctypes.byref(u), ctypes.byref(ue), ctypes.byref(mu), ctypes.byref(lam)),
+           "gs_fem_info")
+    return u.value, ue.value, mu.value, lam.value
+
+
+def gs_fem_export_rest(ctx, fem, T, V):
+    """(w (T, 4, 3), vol (T,), mass (V,)) float64 CUDA tensors."""
+    w = torch.empty((T, 4, 3), dtype=torch.float64, device="cuda")
+    vol = torch.empty(T, dtype=torch.float64, device="cuda")
+    mass = torch.empty(V, dtype=torch.float64, device="cuda")
+    _check(lib().gs_fem_export_rest(ctx, fem, _dev(w, torch.float64, "w"), _dev(vol, torch.float64, "vol"),
+                                    _dev(mass, torch.float64, "mass")), "gs_fem_export_rest")
+    return w, vol, mass
+
+
+def gs_fem_energy(ctx, fem, x, xt, grad=None):
+    """E(x) as a float; the gradient written into grad ((V, 3) float64) when given."""
+    e = _D()
+    _check(lib().gs_fem_energy(ctx, fem, _dev(x, torch.float64, "x"), _dev(xt, torch.float64, "xt"), ctypes.byref(e),
+                               _dev(grad, torch.float64, "grad")), "gs_fem_energy")
+    return e.value
+
+
+def gs_fem_triplets(ctx, fem, x, n_entries):
+    """(rows, cols, blocks (n, 3, 3)) CUDA tensors of the Hessian at x."""
+    rows = torch.empty(n_entries, dtype=torch.int32, device="cuda")
+    cols = torch.empty(n_entries, dtype=torch.int32, device="cuda")
+    blocks = torch.empty((n_entries, 3, 3), dtype=torch.float64, device="cuda")
+    _check(lib().gs_fem_triplets(ctx, fem, _dev(x, torch.float64, "x"), _dev(rows, torch.int32, "rows"),
+                                 _dev(cols, torch.int32, "cols"), _dev(blocks, torch.float64, "blocks")),
+           "gs_fem_triplets")
+    return rows, cols, blocks
+
+
+def gs_fem_assemble(ctx, fem, x):
+    h = _P()
+    _check(lib().gs_fem_assemble(ctx, fem, _dev(x, torch.float64, "x"), ctypes.byref(h)), "gs_fem_assemble")
+    return h
+
+
+def gs_fem_refill(ctx, fem, x, mat):
+    _check(lib().gs_fem_refill(ctx, fem, _dev(x, torch.float64, "x"), mat), "gs_fem_refill")
+
+
+def gs_fem_destroy(fem):
+    _check(lib().gs_fem_destroy(fem), "gs_fem_destroy")
+
+
+def gs_mas_refresh(ctx, mas, mat):
+    _check(lib().gs_mas_refresh(ctx, mas, mat), "gs_mas_refresh")
+
+
+def gs_fem_newton(ctx, fem, xt, x, adj_ptr, adj, tol=1e-3, max_newton=50, pcg_tol=1e-6, pcg_max_iter=10_000,
+                  spmv_variant=GS_SPMV_ROW, domain_size=32, max_levels=3, precision=GS_PREC_FP64,
+                  part_rule=GS_PART_RCB, armijo=1e-4, max_halvings=30, raise_on_maxiter=True):
+    """Newton's method from x (overwritten).  Returns (stats dict, energies (iterations + 1,), status)."""
+    o = gs_newton_opts(tol, max_newton, pcg_tol, pcg_max_iter, spmv_variant, domain_size, max_levels, precision,
+                       part_rule, armijo, max_halvings)
+    st = gs_newton_stats()
+    en = np.zeros(max_newton + 1, dtype=np.float64)
+    s = lib().gs_fem_newton(ctx, fem, _dev(xt, torch.float64, "xt"), _dev(x, torch.float64, "x"),
+                            _dev(adj_ptr, torch.int32, "adj_ptr"), _dev(adj, torch.int32, "adj"), ctypes.byref(o),
+                            ctypes.byref(st), en.ctypes.data_as(_P))
+    if s != GS_OK and not (s == GS_ERR_MAXITER and not raise_on_maxiter):
+        raise GsError(s, "gs_fem_newton")
+    stats = dict(iterations=st.iterations, pcg_iterations=st.pcg_iterations, halvings=st.halvings,
+                 converged=bool(st.converged), energy0=st.energy0, energy=st.energy, step_inf=st.step_inf,
+                 ms={k: st.ms[i] for i, k in enumerate(NEWTON_PHASES)})
+    return stats, en[: st.iterations + 1].copy(), s

@@ -200,6 +200,8 @@ struct gs_mat_s {
   // (hi, lo) = (rn(a), rn(a - hi)) floats.
   float2* au_ff = nullptr;    // nnzb * 9
   int32_t* ff_k = nullptr;    // n + 1: k_i - K per row; [n] holds K = max_i k_i
+  const void* pattern_owner = nullptr;  // the elastic body whose fixed pattern this matrix uses (or null)
+  uint64_t pattern_version = 0;        // and that pattern's version
   gs_ctx owner = nullptr;
 };
 

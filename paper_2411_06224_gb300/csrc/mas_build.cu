@@ -423,6 +423,158 @@ __global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restric
   if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
 }
 
+// Level matrices, inverses and the stored forms of the precision for the
+// level structure already in `mas` (the numeric part of the build; the
+// structure depends only on the partition and the graph, so a matrix with
+// new values on the same nodes reuses it).
+static int mas_numeric(gs_ctx ctx, gs_mas mas, gs_mat mat) {
+  cudaStream_t st = ctx->stream;
+  const int L = mas->L;
+  const int N = mas->N;
+  const int32_t n_dom0 = mas->n_domains[0];
+  const int precision = mas->precision;
+  int s;
+  int flags = 0;
+  // level matrices
+  const int ld = 3 * N;
+  LevelPtrs lp{};
+  lp.L = L;
+  lp.N = N;
+  for (int l = 0; l < L; ++l) {
+    double* m = nullptr;
+    size_t bytes = (size_t)mas->n_domains[l] * ld * ld * sizeof(double);
+    if ((s = ctx->alloc((void**)&m, bytes))) return s;
+    mas->inv64.push_back(m);
+    if (cudaMemsetAsync(m, 0, bytes, st) != cudaSuccess) return GS_ERR_CUDA;
+    lp.coarse[l] = mas->coarse[l];
+    lp.mat[l] = m;
+  }
+  if (mat->nnzb > 0)
+    { GS_PROF(ctx, GS_K_MAS_MATRICES); k_scatter_blocks<<<ceil_div(mat->nnzb, 256), 256, 0, st>>>(mat->rid, mat->cid, mat->au, mat->nnzb, lp); }
+  if (L > 1) { GS_PROF(ctx, GS_K_MAS_MATRICES); k_domain_reduce<<<ceil_div((int64_t)n_dom0 * 32, 256), 256, 0, st>>>(mas->remap0, n_dom0, lp); }
+  // inversion jobs: every domain of every level
+  std::vector<int32_t> h_level, h_index;
+  for (int l = 0; l < L; ++l)
+    for (int32_t d = 0; d < mas->n_domains[l]; ++d) h_level.push_back(l), h_index.push_back(d);
+  const int jobs = (int)h_level.size();
+  int32_t* djobs = nullptr;
+  if ((s = ctx->scratch_buf(kSlotMasBuild3, (size_t)jobs * 8 + (L + 1) * 8 + 8 * sizeof(double*) + 64,
+                            (void**)&djobs)))
+    return s;
+  int32_t* d_items = djobs + 2 * jobs;
+  double** d_mats = (double**)(((uintptr_t)(d_items + L + 1) + 15) & ~(uintptr_t)15);
+  std::vector<double*> hm(mas->inv64.begin(), mas->inv64.end());
+  if (cudaMemcpyAsync(djobs, h_level.data(), jobs * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(djobs + jobs, h_index.data(), jobs * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_items, mas->n_items.data(), L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_mats, hm.data(), L * sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return GS_ERR_CUDA;
+  const size_t smem = (size_t)(3 * N) * (3 * N + 1) / 2 * sizeof(double);  // packed lower triangle
+  if (cudaFuncSetAttribute(k_invert_domains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GS_ERR_CUDA;
+  // BF16 form: level 0 keeps its inverse Cholesky factors (rounding W keeps
+  // W^T W positive semi-definite; rounding M^{-1} itself does not once a
+  // domain's condition number passes ~1e3), coarse levels FP32 inverses
+  double* fac0 = nullptr;
+  const int64_t cnt0 = (int64_t)n_dom0 * ld * ld;
+  if (precision == GS_PREC_BF16) {
+    if ((s = ctx->alloc((void**)&fac0, (size_t)std::max<int64_t>(cnt0, 1) * 8))) return s;
+    if (cudaMemsetAsync(fac0, 0, (size_t)cnt0 * 8, st) != cudaSuccess) return GS_ERR_CUDA;
+  }
+  { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
+                                            ctx->d_flags, fac0); }
+  if (precision == GS_PREC_BF16) {
+    void* f = nullptr;
+    s = ctx->alloc(&f, (size_t)std::max<int64_t>(cnt0, 1) * 2);
+    if (s == GS_OK) {
+      mas->inv16.push_back(f);
+      if (cnt0) { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_bf16<<<ceil_div(cnt0, 256), 256, 0, st>>>(fac0, (__nv_bfloat16*)f, cnt0); }
+      s = level0_bf16_prepare(ctx, mas, fac0);
+    }
+    ctx->release(fac0);
+    if (s) return s;
+  }
+  if (precision == GS_PREC_FP64 && (s = level0_f64tc_prepare(ctx, mas))) return s;
+  if (precision == GS_PREC_FP32 || precision == GS_PREC_BF16) {
+    mas->inv32.assign(L, nullptr);
+    for (int l = precision == GS_PREC_BF16 ? 1 : 0; l < L; ++l) {
+      float* f = nullptr;
+      int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
+      if ((s = ctx->alloc((void**)&f, (size_t)cnt * 4))) return s;
+      mas->inv32[l] = f;
+      { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt); }
+    }
+    if (precision == GS_PREC_FP32) {  // level 0 also as packed lower triangles (the streamed apply)
+      const int pitch = ((ld * (ld + 1) / 2 + 3) / 4) * 4;
+      const int64_t cnt = (int64_t)mas->n_domains[0] * pitch;
+      if ((s = ctx->alloc((void**)&mas->inv32p, (size_t)cnt * 4))) return s;
+      { GS_PROF(ctx, GS_K_MAS_INVERT); k_pack_lower_f32<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[0], mas->inv32p, mas->n_domains[0], ld, pitch); }
+    }
+  }
+  // multilevel vector layout for the apply (levels >= 1, padded per domain)
+  mas->vec_off.assign(L, 0);
+  int64_t off = 0;
+  for (int l = 1; l < L; ++l) {
+    mas->vec_off[l] = off;
+    off += (int64_t)mas->n_domains[l] * N;
+  }
+  mas->vec_items = off;
+  // constant tables of the apply: inverse pointers and the coarse domain jobs
+  {
+    std::vector<void*> hp(8, nullptr);
+    for (int l = 0; l < L; ++l)
+      hp[l] = precision == GS_PREC_FP32   ? (void*)mas->inv32[l]
+              : precision == GS_PREC_BF16 ? (l == 0 ? mas->inv16[0] : (void*)mas->inv32[l])
+                                                : (void*)mas->inv64[l];
+    std::vector<int32_t> lev, dom;
+    for (int l = 1; l < L; ++l)
+      for (int32_t d = 0; d < mas->n_domains[l]; ++d) lev.push_back(l), dom.push_back(d);
+    mas->n_coarse_jobs = (int32_t)lev.size();
+    lev.insert(lev.end(), dom.begin(), dom.end());
+    if ((s = ctx->alloc((void**)&mas->d_inv_tab, 8 * sizeof(void*))) ||
+        (s = ctx->alloc((void**)&mas->d_coarse_jobs, std::max<size_t>(lev.size(), 1) * 4)))
+      return s;
+    if (cudaMemcpyAsync(mas->d_inv_tab, hp.data(), 8 * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (!lev.empty() && cudaMemcpyAsync(mas->d_coarse_jobs, lev.data(), lev.size() * 4, cudaMemcpyHostToDevice,
+                                         st) != cudaSuccess))
+      return GS_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
+  if ((s = ctx->take_flags(&flags))) return s;
+  if (flags) return status_from_flags(flags);
+  return GS_OK;
+}
+
+// Releases what mas_numeric made (lazily built copies included).
+static void mas_release_numeric(gs_mas mas) {
+  gs_ctx c = mas->owner;
+  for (auto p : mas->inv64) c->release(p);
+  for (auto p : mas->inv32) c->release(p);
+  for (auto p : mas->inv16) c->release(p);
+  for (auto p : mas->dig64) c->release(p);
+  for (auto p : mas->dig64_exp) c->release(p);
+  c->release(mas->inv32p);
+  c->release(mas->inv16_tc);
+  c->release(mas->d_dig_tab);
+  c->release(mas->d_inv_tab);
+  c->release(mas->d_coarse_jobs);
+  c->release(mas->d_inv32_tab);
+  mas->inv64.clear();
+  mas->inv32.clear();
+  mas->inv16.clear();
+  mas->dig64.clear();
+  mas->dig64_exp.clear();
+  mas->inv32p = nullptr;
+  mas->inv16_tc = nullptr;
+  mas->d_dig_tab = nullptr;
+  mas->d_inv_tab = nullptr;
+  mas->d_coarse_jobs = nullptr;
+  mas->d_inv32_tab = nullptr;
+  mas->vec_off.clear();
+  mas->vec_items = 0;
+  mas->n_coarse_jobs = 0;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -559,117 +711,20 @@ int gs_build_mas(gs_ctx ctx, gs_mat mat, const int32_t* map, int32_t n_dom0, con
     n_real = n_next;
   }
   mas->L = (int)mas->coarse.size();
-  const int L = mas->L;
-  mas->up.resize(L, nullptr);
-  // level matrices
-  const int ld = 3 * N;
-  LevelPtrs lp{};
-  lp.L = L;
-  lp.N = N;
-  for (int l = 0; l < L; ++l) {
-    double* m = nullptr;
-    size_t bytes = (size_t)mas->n_domains[l] * ld * ld * sizeof(double);
-    if ((s = ctx->alloc((void**)&m, bytes))) return fail(s);
-    mas->inv64.push_back(m);
-    if (cudaMemsetAsync(m, 0, bytes, st) != cudaSuccess) return fail(GS_ERR_CUDA);
-    lp.coarse[l] = mas->coarse[l];
-    lp.mat[l] = m;
-  }
-  if (mat->nnzb > 0)
-    { GS_PROF(ctx, GS_K_MAS_MATRICES); k_scatter_blocks<<<ceil_div(mat->nnzb, 256), 256, 0, st>>>(mat->rid, mat->cid, mat->au, mat->nnzb, lp); }
-  if (L > 1) { GS_PROF(ctx, GS_K_MAS_MATRICES); k_domain_reduce<<<ceil_div((int64_t)n_dom0 * 32, 256), 256, 0, st>>>(mas->remap0, n_dom0, lp); }
-  // inversion jobs: every domain of every level
-  std::vector<int32_t> h_level, h_index;
-  for (int l = 0; l < L; ++l)
-    for (int32_t d = 0; d < mas->n_domains[l]; ++d) h_level.push_back(l), h_index.push_back(d);
-  const int jobs = (int)h_level.size();
-  int32_t* djobs = nullptr;
-  if ((s = ctx->scratch_buf(kSlotMasBuild3, (size_t)jobs * 8 + (L + 1) * 8 + 8 * sizeof(double*) + 64,
-                            (void**)&djobs)))
-    return fail(s);
-  int32_t* d_items = djobs + 2 * jobs;
-  double** d_mats = (double**)(((uintptr_t)(d_items + L + 1) + 15) & ~(uintptr_t)15);
-  std::vector<double*> hm(mas->inv64.begin(), mas->inv64.end());
-  if (cudaMemcpyAsync(djobs, h_level.data(), jobs * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(djobs + jobs, h_index.data(), jobs * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d_items, mas->n_items.data(), L * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d_mats, hm.data(), L * sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return fail(GS_ERR_CUDA);
-  const size_t smem = (size_t)(3 * N) * (3 * N + 1) / 2 * sizeof(double);  // packed lower triangle
-  if (cudaFuncSetAttribute(k_invert_domains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return fail(GS_ERR_CUDA);
-  // BF16 form: level 0 keeps its inverse Cholesky factors (rounding W keeps
-  // W^T W positive semi-definite; rounding M^{-1} itself does not once a
-  // domain's condition number passes ~1e3), coarse levels FP32 inverses
-  double* fac0 = nullptr;
-  const int64_t cnt0 = (int64_t)n_dom0 * ld * ld;
-  if (opts->precision == GS_PREC_BF16) {
-    if ((s = ctx->alloc((void**)&fac0, (size_t)std::max<int64_t>(cnt0, 1) * 8))) return fail(s);
-    if (cudaMemsetAsync(fac0, 0, (size_t)cnt0 * 8, st) != cudaSuccess) return fail(GS_ERR_CUDA);
-  }
-  { GS_PROF(ctx, GS_K_MAS_INVERT); k_invert_domains<<<jobs, 256, smem, st>>>(d_mats, mas->remap0, n_dom0, djobs, djobs + jobs, d_items, N,
-                                            ctx->d_flags, fac0); }
-  if (opts->precision == GS_PREC_BF16) {
-    void* f = nullptr;
-    s = ctx->alloc(&f, (size_t)std::max<int64_t>(cnt0, 1) * 2);
-    if (s == GS_OK) {
-      mas->inv16.push_back(f);
-      if (cnt0) { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_bf16<<<ceil_div(cnt0, 256), 256, 0, st>>>(fac0, (__nv_bfloat16*)f, cnt0); }
-      s = level0_bf16_prepare(ctx, mas, fac0);
-    }
-    ctx->release(fac0);
-    if (s) return fail(s);
-  }
-  if (opts->precision == GS_PREC_FP64 && (s = level0_f64tc_prepare(ctx, mas))) return fail(s);
-  if (opts->precision == GS_PREC_FP32 || opts->precision == GS_PREC_BF16) {
-    mas->inv32.assign(L, nullptr);
-    for (int l = opts->precision == GS_PREC_BF16 ? 1 : 0; l < L; ++l) {
-      float* f = nullptr;
-      int64_t cnt = (int64_t)mas->n_domains[l] * ld * ld;
-      if ((s = ctx->alloc((void**)&f, (size_t)cnt * 4))) return fail(s);
-      mas->inv32[l] = f;
-      { GS_PROF(ctx, GS_K_MAS_INVERT); k_to_float<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[l], f, cnt); }
-    }
-    if (opts->precision == GS_PREC_FP32) {  // level 0 also as packed lower triangles (the streamed apply)
-      const int pitch = ((ld * (ld + 1) / 2 + 3) / 4) * 4;
-      const int64_t cnt = (int64_t)mas->n_domains[0] * pitch;
-      if ((s = ctx->alloc((void**)&mas->inv32p, (size_t)cnt * 4))) return fail(s);
-      { GS_PROF(ctx, GS_K_MAS_INVERT); k_pack_lower_f32<<<ceil_div(cnt, 256), 256, 0, st>>>(mas->inv64[0], mas->inv32p, mas->n_domains[0], ld, pitch); }
-    }
-  }
-  // multilevel vector layout for the apply (levels >= 1, padded per domain)
-  mas->vec_off.assign(L, 0);
-  int64_t off = 0;
-  for (int l = 1; l < L; ++l) {
-    mas->vec_off[l] = off;
-    off += (int64_t)mas->n_domains[l] * N;
-  }
-  mas->vec_items = off;
-  // constant tables of the apply: inverse pointers and the coarse domain jobs
-  {
-    std::vector<void*> hp(8, nullptr);
-    for (int l = 0; l < L; ++l)
-      hp[l] = opts->precision == GS_PREC_FP32   ? (void*)mas->inv32[l]
-              : opts->precision == GS_PREC_BF16 ? (l == 0 ? mas->inv16[0] : (void*)mas->inv32[l])
-                                                : (void*)mas->inv64[l];
-    std::vector<int32_t> lev, dom;
-    for (int l = 1; l < L; ++l)
-      for (int32_t d = 0; d < mas->n_domains[l]; ++d) lev.push_back(l), dom.push_back(d);
-    mas->n_coarse_jobs = (int32_t)lev.size();
-    lev.insert(lev.end(), dom.begin(), dom.end());
-    if ((s = ctx->alloc((void**)&mas->d_inv_tab, 8 * sizeof(void*))) ||
-        (s = ctx->alloc((void**)&mas->d_coarse_jobs, std::max<size_t>(lev.size(), 1) * 4)))
-      return fail(s);
-    if (cudaMemcpyAsync(mas->d_inv_tab, hp.data(), 8 * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        (!lev.empty() && cudaMemcpyAsync(mas->d_coarse_jobs, lev.data(), lev.size() * 4, cudaMemcpyHostToDevice,
-                                         st) != cudaSuccess))
-      return fail(GS_ERR_CUDA);
-  }
-  if (cudaGetLastError() != cudaSuccess) return fail(GS_ERR_CUDA);
-  if ((s = ctx->take_flags(&flags))) return fail(s);
-  if (flags) return fail(status_from_flags(flags));
+  mas->up.resize(mas->L, nullptr);
+  if ((s = mas_numeric(ctx, mas, mat))) return fail(s);
   *out = mas;
   return GS_OK;
+}
+
+int gs_mas_refresh(gs_ctx ctx, gs_mas mas, gs_mat mat) {
+  GS_CHECK(ctx && mas && mat, GS_ERR_INVALID, "gs_mas_refresh: null argument");
+  GS_CHECK(mas->owner == ctx, GS_ERR_INVALID, "gs_mas_refresh: preconditioner of another context");
+  GS_CHECK(mat->n == mas->n, GS_ERR_INVALID, "gs_mas_refresh: matrix has %d block rows, preconditioner %d", mat->n,
+           mas->n);
+  GS_CUDA(cudaSetDevice(ctx->device));
+  mas_release_numeric(mas);
+  return mas_numeric(ctx, mas, mat);
 }
 
 int gs_mas_info(gs_mas mas, int32_t* n_levels, int32_t* n_items) {

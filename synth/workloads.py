@@ -181,3 +181,59 @@ def uneven_batch(n_sys=64, v_range=(1_000, 50_000), e_range=(1e5, 1e9), contact_
         systems.append(make_tet_system(n, E=E, n_contacts=max(1, int(contact_frac * n ** 3)),
                                        contact_mode="random", seed=seed * 1000 + s))
     return concat_systems(systems)
+
+
+@dataclass
+class ElasticScene:
+    """Inputs of one implicit-Euler step of a tet cube (positions, springs,
+    graph); the element arithmetic is left to the solver under test."""
+
+    n_grid: int
+    X: np.ndarray  # rest positions (V, 3)
+    tets: np.ndarray  # int32 (T, 4)
+    x: np.ndarray  # deformed start positions (V, 3)
+    xt: np.ndarray  # predicted positions x + dt v (V, 3)
+    pairs: np.ndarray  # int32 (P, 2) spring vertex pairs
+    K: np.ndarray  # (P, 3, 3) k n n^T
+    rest: np.ndarray  # (P, 3) rest offsets X_i - X_j
+    adj_ptr: np.ndarray
+    adj: np.ndarray
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_vertices(self):
+        return self.X.shape[0]
+
+
+def make_elastic_scene(n, E=1e5, nu=0.4, rho=1000.0, dt=0.01, n_springs=0, k_range=(1e2, 1e4), omega=1.0,
+                       flip=0, seed=3000):
+    """n^3 tet cube: rest X jittered N(0, 0.05 h); start x = (I + G) X + N(0, 0.02 h)
+    with G_ij ~ U(-0.1, 0.1) (the stiffness-sweep recipe); velocity a rigid
+    rotation with angular velocity N(0, omega^2) per axis about the centre, so
+    xt = x + dt v; springs: random distinct vertex pairs with K = k n n^T (n
+    uniform on the sphere, k log-uniform in k_range) at their rest offsets.
+    flip > 0 reflects every flip-th vertex of x through the plane z = centre
+    (inverted elements: the projection's hard case)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n - 1)
+    X, tets = tet_cube(n, rng, jitter=0.05)
+    G = rng.uniform(-0.1, 0.1, (3, 3))
+    x = X @ (np.eye(3) + G).T + rng.normal(0.0, 0.02 * h, X.shape)
+    if flip:
+        c = x[:, 2].mean()
+        x[::flip, 2] = 2 * c - x[::flip, 2]
+    w = rng.normal(0.0, omega, 3)
+    xt = x + dt * np.cross(w, x - x.mean(axis=0))
+    V = X.shape[0]
+    if n_springs:
+        pairs = random_pairs(rng, V, n_springs)
+        nvec = rng.normal(size=(n_springs, 3))
+        nvec /= np.linalg.norm(nvec, axis=1, keepdims=True)
+        k = np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1]), n_springs))
+        K = k[:, None, None] * nvec[:, :, None] * nvec[:, None, :]
+        rest = X[pairs[:, 0]] - X[pairs[:, 1]]
+    else:
+        pairs, K, rest = np.zeros((0, 2), np.int32), np.zeros((0, 3, 3)), np.zeros((0, 3))
+    ptr, adj = adjacency_csr(V, tet_edges(tets))
+    return ElasticScene(n, X, tets.astype(np.int32), x, xt, pairs.astype(np.int32), K, rest, ptr, adj,
+                        dict(n=n, E=E, nu=nu, rho=rho, dt=dt, n_springs=n_springs, seed=seed))
