@@ -40,6 +40,13 @@ TOL = 1e-6
 METRIC = "Newton solves/s to 1e-6 rel. residual (FP64 vs mixed MAS-PCG); SpMV HBM GB/s"
 
 
+def _json_scalar(o):
+    """numpy scalars in the output line as plain numbers."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"not serialisable: {type(o).__name__}")
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -77,6 +84,12 @@ def parse():
                    help="timed solves per variant of the partition / level comparison (0 = skip)")
     p.add_argument("--no-config1", dest="config1", action="store_false",
                    help="skip the plain FP64 solve of the 16^3 cube (forms.plain16)")
+    p.add_argument("--no-newton", dest="newton", action="store_false",
+                   help="skip the Newton loop on the elastic cube (forms.newton)")
+    p.add_argument("--element-probe", type=int, default=0, metavar="GRID",
+                   help="instead of the solve benchmark: build the Newton form's elastic cube at GRID^3, assemble "
+                        "its Hessian once and refill it --refills times (a short run for ncu captures)")
+    p.add_argument("--refills", type=int, default=3)
     p.add_argument("--micro", action="store_true",
                    help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
     p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)  # worker mode
@@ -196,6 +209,25 @@ def oracle_full_plain16(spec):
     print(json.dumps({"samples": out, "host": host_info()}))
 
 
+def oracle_elastic_sample(spec):
+    """Worker: the oracle's element Hessians (PSD projection by a numeric 9x9
+    eigendecomposition, pullback, triplets with masses: elastic.system_triplets)
+    and its energy and gradient on the first `tets` tets of the elastic scene,
+    single thread; prints seconds (JSON)."""
+    from oracle import elastic
+    from synth.workloads import make_elastic_scene
+
+    s_ = make_elastic_scene(spec["grid"], n_springs=0, omega=10.0, seed=spec["seed"])
+    tets = s_.tets[: spec["tets"]]
+    t0 = time.perf_counter()
+    elastic.system_triplets(s_.X, s_.x, tets, spec["E"], spec["nu"], spec["rho"], spec["dt"])
+    t1 = time.perf_counter()
+    elastic.energy_and_gradient(s_.X, s_.x, tets, spec["E"], spec["nu"])
+    t2 = time.perf_counter()
+    print(json.dumps({"tets": int(len(tets)), "t_hessian": t1 - t0, "t_energy_gradient": t2 - t1,
+                      "host": host_info()}))
+
+
 def run_oracle_sample(grid, Es, samples, iters=20, procs=1, cycle=False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -285,13 +317,14 @@ def measured_peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
-def recorded_traffic(kernel, workload):
+def recorded_traffic(kernel, workload, table="dram_traffic.md"):
     """DRAM bytes per launch of `kernel` on `workload` as recorded from an ncu
-    capture in profiles/dram_traffic.md, if the kernel's source file still has
-    the hash recorded with it (else None: the kernel changed since)."""
+    capture in profiles/dram_traffic.md (or the first value column of another
+    table of the same layout), if the kernel's source file still has the hash
+    recorded with it (else None: the kernel changed since)."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    path = os.path.join(ROOT, "profiles", table)
     if not os.path.exists(path):
         return None
     for ln in open(path):
@@ -477,12 +510,187 @@ def config1_form(args, B, dev, variant, clk):
     return out
 
 
+def element_probe(args):
+    """The Newton form's elastic cube at --element-probe vertices per edge:
+    body created (element keys sorted), springs set, Hessian assembled at the
+    start positions, then refilled --refills times; prints the counts."""
+    import numpy as np
+    import torch
+
+    from paper_2411_06224_gb300.build import build
+    from synth.workloads import make_elastic_scene
+
+    build()
+    from paper_2411_06224_gb300 import binding as B
+
+    n = args.element_probe
+    s_ = make_elastic_scene(n, n_springs=max(1, 200_000 * n ** 3 // 64 ** 3), omega=10.0, seed=3000 + n)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    ctx = B.gs_create(0)
+    f = B.gs_fem_create(ctx, t(s_.X, torch.float64), t(s_.tets, torch.int32), 1e5, 0.4, 1000.0, 0.01)
+    B.gs_fem_set_springs(ctx, f, t(s_.pairs, torch.int32), t(s_.K, torch.float64), t(s_.rest, torch.float64))
+    x0 = t(s_.x, torch.float64)
+    m = B.gs_fem_assemble(ctx, f, x0)
+    for _ in range(args.refills):
+        B.gs_fem_refill(ctx, f, x0, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"tets": int(len(s_.tets)), "vertices": s_.n_vertices, "stored_blocks": B.gs_fem_info(f)[0],
+                      "refills": args.refills}))
+    B.gs_mat_destroy(m)
+    B.gs_fem_destroy(f)
+    B.gs_destroy(ctx)
+
+
+def newton_form(args, B, dev, clk):
+    """Newton's method on the implicit-Euler step of the tet cube (stable
+    Neo-Hookean, E = 1e5, nu = 0.4, rho = 1000, dt = 0.01; springs on random
+    vertex pairs standing in for contacts): element Hessians on the device,
+    values reduced through the pattern sorted once, MAS built at the first
+    step and refreshed after, MAS-PCG to 1e-6 per step, Armijo backtracking.
+    Also: the numeric assembly (no sort) against re-sorting every step, and
+    the element-Hessian kernel's roofline line."""
+    import numpy as np
+    import torch
+
+    from synth.workloads import make_elastic_scene
+
+    E_, NU, RHO, DT = 1e5, 0.4, 1000.0, 0.01
+    n_springs = max(1, 200_000 * args.grid ** 3 // 64 ** 3)
+    seed = 3000 + args.grid
+    s_ = make_elastic_scene(args.grid, E=E_, n_springs=n_springs, omega=10.0, seed=seed)
+    V, T = s_.n_vertices, len(s_.tets)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    X, tets, x0, xt = t(s_.X, torch.float64), t(s_.tets, torch.int32), t(s_.x, torch.float64), t(s_.xt, torch.float64)
+    pairs, K, rest = t(s_.pairs, torch.int32), t(s_.K, torch.float64), t(s_.rest, torch.float64)
+    ptr, adj = t(s_.adj_ptr, torch.int32), t(s_.adj, torch.int32)
+    stream = torch.cuda.current_stream()
+    ctx = B.gs_create(dev.index or 0, stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"tet cube {args.grid}^3 ({V} vertices, {T} tets), SNH E=1e5 nu=0.4, rho=1000, dt=0.01, "
+                       f"{n_springs} springs k n n^T (k 1e2-1e4) on random vertex pairs, rotation 10 rad/s per axis; "
+                       "Newton tol |d|_inf <= 1e-3 dt, PCG tol 1e-6, FP64 MAS N=32, 3 levels, float-float SpMV"}
+    f = None
+    try:
+        torch.cuda.synchronize()
+        a, b_ = ev(), ev()
+        a.record(stream)
+        f = B.gs_fem_create(ctx, X, tets, E_, NU, RHO, DT)
+        B.gs_fem_set_springs(ctx, f, pairs, K, rest)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        U, Ue, _, _ = B.gs_fem_info(f)
+        out["symbolic_ms"] = a.elapsed_time(b_)
+        out["stored_blocks"], out["element_stored_blocks"] = U, Ue
+        # numeric assembly through the fixed pattern vs a full re-sort of the same triplets
+        m = B.gs_fem_assemble(ctx, f, x0)
+        reps = 5
+        for _ in range(2):
+            B.gs_fem_refill(ctx, f, x0, m)
+        torch.cuda.synchronize()
+        B.gs_profile_begin(ctx, [B.GS_K_ELEMENT, B.GS_K_ASSEMBLE])
+        a.record(stream)
+        for _ in range(reps):
+            B.gs_fem_refill(ctx, f, x0, m)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        launches, kms = B.gs_profile_end(ctx)
+        ms_refill = a.elapsed_time(b_) / reps
+        n_in = 10 * T + V + 3 * n_springs
+        r, c, bl = B.gs_fem_triplets(ctx, f, x0, n_in)
+        m2 = B.gs_assemble(ctx, V, r, c, bl)
+        B.gs_mat_destroy(m2)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            r, c, bl = B.gs_fem_triplets(ctx, f, x0, n_in)
+            m2 = B.gs_assemble(ctx, V, r, c, bl)
+            B.gs_mat_destroy(m2)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms_resort = a.elapsed_time(b_) / reps
+        del r, c, bl
+        B.gs_mat_destroy(m)
+        n_el = int(max(launches[B.GS_K_ELEMENT] // reps, 1))
+        t_hess = kms[B.GS_K_ELEMENT] / 1e3 / reps  # both kernels of one refill
+        props = torch.cuda.get_device_properties(dev)
+        sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
+        fp64_peak = props.multi_processor_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        # algorithmic bytes per tet: 4 x 24 B of x gathered, 96 B w, 8 B vol, 16 B tets read; 10 x 72 B written
+        el_bytes = T * (96 + 96 + 8 + 16 + 720) + V * 80
+        wl = f"tet{args.grid}"
+        flops = recorded_traffic("k_element_hessians", wl, table="fp64_ops.md")
+        line = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
+                "achieved": flops / t_hess / 1e12 if flops else None,
+                "frac": flops / t_hess / 1e12 / fp64_peak if flops else None,
+                "traffic": recorded_traffic("k_element_hessians", wl),
+                "flops_per_launch": flops, "bytes_per_launch": el_bytes,
+                "hbm_gbs": el_bytes / t_hess / 1e9, "hbm_frac": el_bytes / t_hess / 1e9 / hbm,
+                "avg_launch_ms": t_hess * 1e3, "tets_per_s": T / t_hess, "launches_per_refill": n_el,
+                "kernel": "k_element_hessians (SNH, analytic-eigensystem PSD projection, pullback; FP64) + k_mass_blocks",
+                "flops_source": "FP64 operations per launch (2 per DFMA) from an ncu capture, profiles/fp64_ops.md"}
+        out["kernels"] = {"element_hessians": line}
+        out["assembly"] = {"ms_numeric_refill": ms_refill, "ms_resort_every_step": ms_resort,
+                           "speedup": ms_resort / ms_refill,
+                           "ms_refill_element_kernels": kms[B.GS_K_ELEMENT] / reps,
+                           "ms_refill_reduction": kms[B.GS_K_ASSEMBLE] / reps,
+                           "resort": "gs_fem_triplets (same element kernel, triplets copied out) + gs_assemble "
+                                     "(key encode, radix sort, run flags, scan, segmented reduction)"}
+        # the Newton loop
+        def newton_run():
+            x = x0.clone()
+            st, en, status = B.gs_fem_newton(ctx, f, xt, x, ptr, adj, tol=1e-3, max_newton=50, pcg_tol=TOL,
+                                             pcg_max_iter=20000, spmv_variant=B.GS_SPMV_ROW_FF, domain_size=32,
+                                             max_levels=3, raise_on_maxiter=False)
+            return st, en, status
+
+        newton_run()  # warm-up
+        torch.cuda.synchronize()
+        a.record(stream)
+        st, en, status = newton_run()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b_) / 1e3
+        out.update({"value": 1.0 / sec, "unit": "Newton solves/s (complete implicit steps)",
+                    "ms_per_solve": sec * 1e3, "newton_steps": st["iterations"],
+                    "newton_steps_per_s": st["iterations"] / sec, "converged": st["converged"],
+                    "status": int(status), "pcg_iterations_total": st["pcg_iterations"],
+                    "line_search_halvings": st["halvings"], "energy": [float(e) for e in en],
+                    "phase_ms": st["ms"]})
+    finally:
+        if f is not None:
+            B.gs_fem_destroy(f)
+        B.gs_destroy(ctx)
+    if not args.no_cpu_baseline:
+        try:
+            k = min(T, 20000)
+            env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                       CUDA_VISIBLE_DEVICES="")
+            spec = {"kind": "elastic", "grid": args.grid, "seed": seed, "tets": k, "E": E_, "nu": NU, "rho": RHO,
+                    "dt": DT}
+            r_ = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", json.dumps(spec)],
+                                env=env, capture_output=True, text=True, timeout=1800)
+            res = json.loads(r_.stdout.strip().splitlines()[-1])
+            rate = res["tets"] / res["t_hessian"]
+            out["kernels"]["element_hessians"]["cpu_baseline"] = {
+                "value": rate, "unit": "element Hessians/s", "cores": 1, "kind": "oracle",
+                "sample": (f"oracle elastic.system_triplets on the first {res['tets']} tets of this scene, one host "
+                           f"core ({res['host']['cpu_model']}): {res['t_hessian']:.2f} s; energy and gradient "
+                           f"{res['t_energy_gradient']:.2f} s"),
+                "device_ratio": (T / t_hess) / rate}
+        except Exception as e:  # noqa: BLE001
+            out["kernels"]["element_hessians"]["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
+    return out
+
+
 def main():
     args = parse()
     if args.oracle_sample:
         spec = json.loads(args.oracle_sample)
         if spec.get("kind") == "plain16":
             oracle_full_plain16(spec)
+        elif spec.get("kind") == "elastic":
+            oracle_elastic_sample(spec)
         else:
             oracle_sample(spec)
         return
@@ -493,6 +701,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.micro:
         return micro(args)
+    if args.element_probe:
+        return element_probe(args)
 
     import numpy as np
     import torch
@@ -539,11 +749,12 @@ def main():
     # its own host thread, so the FP64-pipe-bound SpMV of one system overlaps
     # the HBM- and tensor-bound MAS apply of another.
     n_lanes = (args.streams if args.streams > 0 and args.queue else len(dsys)) if args.lanes else 1
-    lane_streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)] if args.lanes else [stream]
-    lane_ctx = [B.gs_create(local, s_) for s_ in lane_streams] if args.lanes else [ctx]
+    multi = n_lanes > 1  # one lane is the main context on the main stream
+    lane_streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)] if multi else [stream]
+    lane_ctx = [B.gs_create(local, s_) for s_ in lane_streams] if multi else [ctx]
     # solution buffers per lane and system: two steps' solves of one system
     # may run at once on two lanes
-    lane_xs = [[torch.zeros_like(b) for _ in dsys] for _ in range(n_lanes)] if args.lanes else [[x] * len(dsys)]
+    lane_xs = [[torch.zeros_like(b) for _ in dsys] for _ in range(n_lanes)] if multi else [[x] * len(dsys)]
     last_lane = {}  # system -> lane of its latest finished solve
     pool = ThreadPoolExecutor(max_workers=n_lanes)
 
@@ -1025,6 +1236,14 @@ def main():
         except B.GsError as e:
             plain16 = {"error": str(e)[:300]}
 
+    # Newton's method with device element Hessians and the fixed pattern
+    newton_f = None
+    if args.newton:
+        try:
+            newton_f = newton_form(args, B, dev, clk)
+        except B.GsError as e:
+            newton_f = {"error": str(e)[:300]}
+
     # roofline of the dominant kernel class
     apply_line, spmv_line = kernel_lines(B, ctx, dev, clk, args.spmv, prec, args.nrhs, N, V, nnzb, ndom, mp,
                                          (launches, kms), (launches_1, ms_1),
@@ -1069,7 +1288,7 @@ def main():
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
         "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth, "plain16": plain16,
-                  "partitions": partitions},
+                  "partitions": partitions, "newton": newton_f},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),
@@ -1103,7 +1322,7 @@ def main():
             line["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
     B.gs_destroy(ctx)
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, default=_json_scalar))
     if world > 1:
         dist.destroy_process_group()
 
@@ -1265,7 +1484,7 @@ def reference_arm(args, rank, world):
                          "host": host},
         "e2e": {"value": value, "unit": "Newton solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    print(json.dumps(line, default=_json_scalar))
 
 
 if __name__ == "__main__":

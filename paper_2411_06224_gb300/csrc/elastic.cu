@@ -89,15 +89,19 @@ namespace gs {
 namespace fem {
 
 // ------------------------------------------------------------------ 3x3 math
-// One cyclic-Jacobi rotation in the (p, q) plane: A <- J^T A J, V <- V J.
+// One cyclic-Jacobi rotation in the (p, q) plane: A <- J^T A J, Q <- Q J.
+// With th = (A_qq - A_pp) / 2 the rotation tangent is the smaller root of
+// t^2 + 2 (th / A_pq) t - 1 = 0, written as sgn(th) A_pq / (|th| + hypot(th, A_pq))
+// (one division, no overflow of th / A_pq); c = 1 / sqrt(1 + t^2), s = t c.
 template <int p, int q>
 __device__ __forceinline__ void jacobi_rotate(double (&A)[3][3], double (&Q)[3][3]) {
   constexpr int r = 3 - p - q;
   const double apq = A[p][q];
-  if (apq == 0.0) return;
-  const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-  const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  const double c = 1.0 / sqrt(1.0 + t * t);
+  const double th = 0.5 * (A[q][q] - A[p][p]);
+  const double h = sqrt(th * th + apq * apq);
+  if (apq == 0.0 || h == 0.0) return;
+  const double t = (th >= 0.0 ? apq : -apq) / (fabs(th) + h);
+  const double c = rsqrt(1.0 + t * t);
   const double s = t * c;
   A[p][p] -= t * apq;
   A[q][q] += t * apq;
@@ -148,9 +152,10 @@ __device__ __forceinline__ void swap_pair(double (&A)[3][3], double (&Q)[3][3]) 
 template <int p, int q>
 __device__ __forceinline__ void givens(double (&B)[3][3], double (&U)[3][3]) {
   const double a = B[p][p], b = B[q][p];
-  const double rr = sqrt(a * a + b * b);
-  if (rr == 0.0) return;
-  const double c = a / rr, s = b / rr;
+  const double n2 = a * a + b * b;
+  if (n2 == 0.0) return;
+  const double inv = rsqrt(n2);
+  const double c = a * inv, s = b * inv;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double bp = B[p][k], bq = B[q][k];
@@ -380,44 +385,68 @@ __global__ void __launch_bounds__(128) k_element_hessians(const double* __restri
     dk[k] = 0.5 * (tw + fl);
     ok[k] = 0.5 * (fl - tw);
   }
-  // z_a = V^T w_a
+  // z_a = vol^(1/2) V^T w_a (the volume split over both factors of each block)
+  const double sv = sqrt(vol[t]);
   double z[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) z[a][j] = wl[a][0] * Vm[0][j] + wl[a][1] * Vm[1][j] + wl[a][2] * Vm[2][j];
-  const double vt = vol[t];
-  double* dst = out + (size_t)t * 90;
+    for (int j = 0; j < 3; ++j)
+      z[a][j] = sv * (wl[a][0] * Vm[0][j] + wl[a][1] * Vm[1][j] + wl[a][2] * Vm[2][j]);
+  // The projected F-Hessian rotated back by U, kept per pair of D-columns:
+  // G[c][c'][r][r'] = sum_{i,i'} U[r][i] H_D+[(i,c),(i',c')] U[r'][i'].
+  // Diagonal (c = c'): U diag(e) U^T with e_i = Ps[c][c] for i = c, else the
+  // pair block's diagonal dk; off-diagonal: Ps[c][c'] u_c u_c'^T +
+  // ok u_c' u_c^T, and G[c'][c] = G[c][c']^T.
+  double Gd[3][3][3], Go[3][3][3];  // Gd[c] (symmetric); Go[0] = G[0][1], Go[1] = G[0][2], Go[2] = G[1][2]
 #pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    int a, b;
-    pair_nodes(p, a, b);
-    double Hy[3][3];
+  for (int c = 0; c < 3; ++c) {
+    double e[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) e[i] = i == c ? Ps[c][c] : dk[3 - i - c];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Hy[i][j] = Ps[i][j] * z[a][i] * z[b][j];
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
-      Hy[i][i] += dk[k] * z[a][j] * z[b][j];
-      Hy[j][j] += dk[k] * z[a][i] * z[b][i];
-      Hy[i][j] += ok[k] * z[a][j] * z[b][i];
-      Hy[j][i] += ok[k] * z[a][i] * z[b][j];
-    }
-    double Tm[3][3];  // Hy U^T
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Tm[i][j] = Hy[i][0] * U[j][0] + Hy[i][1] * U[j][1] + Hy[i][2] * U[j][2];
-    const bool tr = v[a] > v[b];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double h = vt * (U[i][0] * Tm[0][j] + U[i][1] * Tm[1][j] + U[i][2] * Tm[2][j]);
-        dst[9 * p + (tr ? 3 * j + i : 3 * i + j)] = h;
+      for (int q = r; q < 3; ++q) {
+        const double g = e[0] * U[r][0] * U[q][0] + e[1] * U[r][1] * U[q][1] + e[2] * U[r][2] * U[q][2];
+        Gd[c][r][q] = g;
+        Gd[c][q][r] = g;
       }
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int c = m == 2 ? 1 : 0, c2 = m == 0 ? 1 : 2;
+    const double ps = Ps[c][c2], o = ok[3 - c - c2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Go[m][r][q] = ps * U[r][c] * U[q][c2] + o * U[r][c2] * U[q][c];
+  }
+  double* dst = out + (size_t)t * 90;
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    // Ma[c'] = sum_c z_a[c] G[c][c']
+    double Ma[3][3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        Ma[0][r][q] = z[a][0] * Gd[0][r][q] + z[a][1] * Go[0][q][r] + z[a][2] * Go[1][q][r];
+        Ma[1][r][q] = z[a][0] * Go[0][r][q] + z[a][1] * Gd[1][r][q] + z[a][2] * Go[2][q][r];
+        Ma[2][r][q] = z[a][0] * Go[1][r][q] + z[a][1] * Go[2][r][q] + z[a][2] * Gd[2][r][q];
+      }
+#pragma unroll
+    for (int b = a; b < 4; ++b, ++p) {
+      const bool tr = v[a] > v[b];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const double h = z[b][0] * Ma[0][r][q] + z[b][1] * Ma[1][r][q] + z[b][2] * Ma[2][r][q];
+          dst[9 * p + (tr ? 3 * q + r : 3 * r + q)] = h;
+        }
+    }
   }
 }
 
