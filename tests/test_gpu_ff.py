@@ -181,9 +181,13 @@ def test_ff_pcg_converges_like_oracle(B, ctx, name, N, L):
 
 @pytest.mark.parametrize("k", [1, 5, 25])
 def test_ff_pcg_fixed_iterations_follow_oracle_recurrence(B, ctx, k):
-    # Along the same Krylov recurrence the float-float products perturb each
-    # step by about 1e-14 relative; after k steps the iterate still agrees
-    # entry by entry well inside 1e-9.
+    # Along the same Krylov recurrence every product differs from the exact
+    # one by the float-float rounding (measured up to 1.75e-13 (|A||x|)_i,
+    # about 1e3 times FP64's), and CG amplifies per-step differences: on this
+    # E = 1e8 cube a relative perturbation of 1e-16 per product already moves
+    # the 25th iterate by 1e-10.  So the bound is the FP64 path's 1e-9, or ten
+    # times the oracle's own spread when its products are perturbed by
+    # 2e-13 (|A||x|)_i with seeded random signs, whichever is larger.
     bt = _Built(B, ctx, case("cube11"), 32, 3)
     V, nrhs = bt.V, 3
     b = rhs(3 * V, nrhs)
@@ -193,8 +197,18 @@ def test_ff_pcg_fixed_iterations_follow_oracle_recurrence(B, ctx, k):
     assert st == B.GS_ERR_MAXITER and list(it) == [k] * nrhs
     mv = lambda v: pcg.spmv(bt.rid, bt.cid, bt.au, v.reshape(-1, 3)).ravel()
     x0, _, _ = pcg.pcg(mv, lambda v: bt.omas(v), b, fixed_iters=k)
+    rng = np.random.default_rng(77)
+    absa = np.abs(bt.au)
+
+    def mv_perturbed(v):
+        ab = pcg.spmv(bt.rid, bt.cid, absa, np.abs(v).reshape(-1, 3)).ravel()
+        return mv(v) + 2e-13 * ab * rng.uniform(-1.0, 1.0, size=ab.shape)
+
+    x1, _, _ = pcg.pcg(mv_perturbed, lambda v: bt.omas(v), b, fixed_iters=k)
     xg = x.cpu().numpy()
     for q in range(nrhs):
         rms = np.sqrt(np.mean(x0[q] ** 2))
-        assert np.all(np.abs(xg[q] - x0[q]) <= 1e-9 * (np.abs(x0[q]) + rms)), q
+        spread = np.max(np.abs(x1[q] - x0[q]) / (np.abs(x0[q]) + rms))
+        tol = max(1e-9, 10.0 * spread)
+        assert np.all(np.abs(xg[q] - x0[q]) <= tol * (np.abs(x0[q]) + rms)), (q, tol)
     bt.close()
