@@ -84,6 +84,9 @@ def parse():
                    help="timed solves per variant of the partition / level comparison (0 = skip)")
     p.add_argument("--no-config1", dest="config1", action="store_false",
                    help="skip the plain FP64 solve of the 16^3 cube (forms.plain16)")
+    p.add_argument("--no-abd", dest="abd", action="store_false",
+                   help="skip the differentiation form on the 100^3 + 2,000-body coupled scene")
+    p.add_argument("--abd-steps", type=int, default=2, help="timed steps of the coupled-scene form")
     p.add_argument("--no-newton", dest="newton", action="store_false",
                    help="skip the Newton loop on the elastic cube (forms.newton)")
     p.add_argument("--element-probe", type=int, default=0, metavar="GRID",
@@ -228,6 +231,40 @@ def oracle_elastic_sample(spec):
                       "host": host_info()}))
 
 
+def oracle_abd_sample(spec):
+    """Worker: the oracle's complete differentiated solve (two-level ABD
+    assembly, 3-level MAS build, forward PCG to 1e-6, adjoint PCG to 1e-6 for
+    L = ||x - x_t||^2, dL/dH on the stored blocks) of a scene of the coupled
+    recipe at spec["n"]^3 vertices, single thread; prints per-phase seconds,
+    iteration counts and sizes (JSON)."""
+    import numpy as np
+
+    from oracle import adjoint, assembly, mas, partition, pcg
+    from synth.abd import make_abd_scene
+
+    n = spec["n"]
+    frac = n ** 3 / 1e6
+    s_ = make_abd_scene(n=n, n_bodies=max(4, round(2000 * frac)), n_contacts=round(500_000 * frac), seed=1005)
+    mp, _ = partition.map_remap(partition.recursive_bisection(s_.X, 32), 32)
+    rng = np.random.default_rng(2005)
+    b = rng.normal(size=(1, 3 * s_.n_red))
+    xt = rng.normal(size=(1, 3 * s_.n_red))
+    t0 = time.perf_counter()
+    rid, cid, au = assembly.assemble_abd(s_.rows, s_.cols, s_.blocks, s_.body_of_node, s_.xbar, s_.n_fem)
+    t1 = time.perf_counter()
+    M = mas.build_mas(mp, 32, 3, s_.adj_ptr, s_.adj, s_.contacts, rid, cid, au)
+    A = pcg.SymmetricMatrix(s_.n_red, rid, cid, au)
+    t2 = time.perf_counter()
+    x, it, _ = pcg.pcg(A, M, b, tol=1e-6)
+    t3 = time.perf_counter()
+    lam, it_a, _ = pcg.pcg(A, M, 2.0 * (x - xt), tol=1e-6)
+    adjoint.block_gradients(rid, cid, x.reshape(1, -1, 3), lam.reshape(1, -1, 3))
+    t4 = time.perf_counter()
+    print(json.dumps({"t_ga": t1 - t0, "t_pa": t2 - t1, "t_fwd": t3 - t2, "t_adj": t4 - t3,
+                      "iters": [int(it[0]), int(it_a[0])], "inputs": int(s_.rows.size), "rows": int(s_.n_red),
+                      "stored": int(rid.size), "host": host_info()}))
+
+
 def run_oracle_sample(grid, Es, samples, iters=20, procs=1, cycle=False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -359,7 +396,8 @@ def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live,
     n_dom0 = ndom
     real0 = np.bincount(mp // N, minlength=n_dom0)
     apply_flops = 2.0 * float(np.sum((3 * real0) ** 2)) * nrhs
-    inv_bytes = (8 if prec == B.GS_PREC_FP64 else 4) * n_dom0 * ld * ld
+    # the method's bytes: each inverse's packed lower triangle, read once per apply
+    inv_bytes = (8 if prec == B.GS_PREC_FP64 else 4) * n_dom0 * ld * (ld + 1) // 2
     apply_bytes = inv_bytes + 2 * 8 * 3 * V * nrhs
     n_off = nnzb - V
     spmv_flops = nrhs * (18.0 * V + 36.0 * n_off)
@@ -376,14 +414,27 @@ def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live,
                 "hbm_gbs": nbytes / tsec / 1e9, "hbm_frac": nbytes / tsec / 1e9 / hbm,
                 "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
 
-    f64tc = (prec == B.GS_PREC_FP64 and nrhs <= 8 and ld % 16 == 0 and B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 1)
+    tune_tc = B.gs_tune_get(ctx, B.GS_TUNE_F64_TC)
+    f64tc = (prec == B.GS_PREC_FP64 and nrhs <= 8 and ld % 16 == 0 and tune_tc in (1, 3))
     if f64tc:
-        # FP64-accurate apply on the BF16 tensor cores: the 7 BF16 digit matrices
-        # of every level-0 inverse (14 B per entry) stream from HBM once per apply,
-        # plus r read and z written (FP64)
-        dig_bytes = 7 * 2 * n_dom0 * ld * ld
+        if tune_tc == 3:
+            # the block lower triangle of every level-0 inverse as 8 base-128
+            # digit bytes per entry (64 B per 8x8 core block) streams from HBM
+            # once per apply, plus r read and z written (FP64)
+            nb = ld // 8
+            dig_bytes = 8 * 64 * (nb * (nb + 1) // 2) * n_dom0
+            kname = "k_f64sym"
+            kdesc = ("k_f64sym (level-0 MAS apply in FP64 accuracy from the symmetric inverses' block lower "
+                     "triangles as base-128 digit bytes, expanded to BF16 in shared memory, on tcgen05, "
+                     "+ prolongation)")
+        else:
+            # the 7 BF16 digit matrices of every level-0 inverse (14 B per entry)
+            dig_bytes = 7 * 2 * n_dom0 * ld * ld
+            kname = "k_level0_f64tc"
+            kdesc = ("k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
+                     "splitting on tcgen05, + prolongation)")
         tc_bytes = dig_bytes + 2 * 8 * 3 * V * nrhs
-        traffic = recorded_traffic("k_level0_f64tc", traffic_key) if traffic_key else None
+        traffic = recorded_traffic(kname, traffic_key) if traffic_key else None
         apply_line = {"bound": "hbm", "achieved": tc_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": tc_bytes / t_apply / 1e9 / hbm, "traffic": traffic,
                       "method_bytes_frac": apply_bytes / t_apply / 1e9 / hbm,
@@ -391,9 +442,16 @@ def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live,
                       "fp64_equivalent_frac_of_fp64_peak": apply_flops / t_apply / 1e12 / fp64_peak_tflops,
                       "flops_per_launch": apply_flops, "bytes_per_launch": tc_bytes,
                       "method_bytes_per_launch": apply_bytes, "avg_launch_ms": t_apply * 1e3,
-                      "kernel": "k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
-                                "splitting on tcgen05, + prolongation)"}
+                      "kernel": kdesc}
         apply_iso_ach = tc_bytes / t_apply_iso / 1e9
+    elif prec == B.GS_PREC_FP32 and nrhs <= 8:
+        # FP32 inverses streamed as packed lower triangles (k_level0_f32_cta)
+        apply_line = {"bound": "hbm", "achieved": apply_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": apply_bytes / t_apply / 1e9 / hbm, "traffic": None,
+                      "flops_per_launch": apply_flops, "bytes_per_launch": apply_bytes,
+                      "avg_launch_ms": t_apply * 1e3,
+                      "kernel": "k_level0_f32_cta (level-0 MAS apply from packed FP32 lower triangles, + prolongation)"}
+        apply_iso_ach = apply_bytes / t_apply_iso / 1e9
     else:
         apply_line = fp64_line(apply_flops, apply_bytes, t_apply, None)
         apply_line["kernel"] = (f"k_domain_product<double,{B.gs_tune_get(ctx, B.GS_TUNE_APPLY_RHS)},1> "
@@ -504,6 +562,136 @@ def config1_form(args, B, dev, variant, clk):
                 "sample": (f"the FP64 numpy/scipy oracle's complete solve of this system on one host core "
                            f"({res['host']['cpu_model']}): assembly {smp['t_ga']:.3f} s, 2-level MAS build "
                            f"{smp['t_pa']:.3f} s, PCG {smp['t_pcg']:.3f} s (iterations {smp['iters']}); last of 3"),
+                "host": res["host"]}
+        except Exception as e:  # noqa: BLE001
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
+    return out
+
+
+def abd_form(args, B, dev, clk):
+    """The differentiation form on the coupled scene: the 100^3 tet cube
+    (1M vertices, E = 1e6) with 2,000 affine bodies and 500k contact pairs
+    (51M full-space input triplets).  One step = two-level hash assembly
+    (gs_assemble_abd), MAS build with FP32 inverses (N = 32, 3 levels; the
+    partition once per mesh), forward PCG to 1e-6 (FP64 PCG and reductions,
+    float-float SpMV), the adjoint solve for L = ||x - x_t||^2 to 1e-6 and
+    dL/dH on the stored blocks (gs_adjoint), inputs resident in HBM, one
+    stream.  `value`: differentiated solves (forward + adjoint) per second."""
+    import numpy as np
+    import torch
+
+    from synth.abd import make_abd_scene
+
+    t_gen = time.time()
+    # the bodies, contacts and graph on the host; the FEM part's stable
+    # Neo-Hookean element blocks and masses (same positions, same recipe)
+    # from the library's element kernel, untimed input generation
+    s_ = make_abd_scene(fem_blocks=False)
+    N, L = 32, 3
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    ctx = B.gs_create(dev.index or 0, torch.cuda.current_stream())
+    p_ = s_.params
+    fem = B.gs_fem_create(ctx, t(s_.X[: s_.n_fem], torch.float64), t(s_.fem_tets, torch.int32), p_["E"], 0.4,
+                          p_["rho"], p_["dt"])
+    n_fem_trip = 10 * s_.fem_tets.shape[0] + s_.n_fem
+    rf, cf, bf = B.gs_fem_triplets(ctx, fem, t(s_.fem_x, torch.float64), n_fem_trip)
+    B.gs_fem_destroy(fem)
+    rows = torch.cat([rf, t(s_.rows, torch.int32)])
+    cols = torch.cat([cf, t(s_.cols, torch.int32)])
+    blocks = torch.cat([bf, t(s_.blocks, torch.float64)])
+    del rf, cf, bf
+    # emission order of a parallel element loop: one seeded shuffle of all inputs
+    perm = torch.randperm(rows.numel(), generator=torch.Generator(device=dev).manual_seed(1005 + 7919), device=dev)
+    rows, cols, blocks = rows[perm].contiguous(), cols[perm].contiguous(), blocks[perm].contiguous()
+    del perm
+    torch.cuda.synchronize()
+    t_gen = time.time() - t_gen
+    mp, nd = B.gs_partition(s_.X, N)
+    d = dict(rows=rows, cols=cols, blocks=blocks,
+             body=t(s_.body_of_node, torch.int32), xbar=t(s_.xbar, torch.float64), map=t(mp, torch.int32),
+             adj_ptr=t(s_.adj_ptr, torch.int32), adj=t(s_.adj, torch.int32), contacts=t(s_.contacts, torch.int32))
+    n_inputs = int(rows.numel())
+    n = s_.n_red
+    rng = np.random.default_rng(2005)
+    b = t(rng.normal(size=(1, 3 * n)), torch.float64)
+    xt = t(rng.normal(size=(1, 3 * n)), torch.float64)
+    x = torch.zeros_like(b)
+    g = torch.empty_like(b)
+    variant = B.GS_SPMV_ROW_FF
+    buf = {}
+
+    def step():
+        mat = B.gs_assemble_abd(ctx, s_.n_nodes, s_.n_fem, s_.n_bodies, d["body"], d["xbar"], d["rows"], d["cols"],
+                                d["blocks"])
+        M = B.gs_build_mas(ctx, mat, d["map"], nd, d["adj_ptr"], d["adj"], d["contacts"], domain_size=N,
+                           max_levels=L, precision=B.GS_PREC_FP32)
+        nnzb = B.gs_mat_info(mat)[1]
+        if "dLdH" not in buf or buf["dLdH"].shape[0] != nnzb:
+            buf["dLdH"] = torch.empty((nnzb, 3, 3), dtype=torch.float64, device=dev)
+        x.zero_()
+        it, _, _ = B.gs_pcg_solve(ctx, mat, M, b, x, nrhs=1, tol=TOL, max_iter=20000, variant=variant)
+        torch.sub(x, xt, out=g).mul_(2.0)  # dL/dx of the caller's loss
+        lam, it_a = B.gs_adjoint(ctx, mat, M, x, g, nrhs=1, tol=TOL, dLdH=buf["dLdH"])
+        B.gs_mas_destroy(M)
+        B.gs_mat_destroy(mat)
+        return [int(it[0]), int(it_a[0])], nnzb
+
+    try:
+        for _ in range(max(args.warmup, 3)):
+            its, nnzb = step()
+        B.gs_profile_begin(ctx, range(B.GS_K_COUNT))
+        step()
+        alone = B.gs_profile_end(ctx)
+        steps = max(args.abd_steps, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.gs_profile_begin(ctx, [B.GS_K_MAS_APPLY_L0, B.GS_K_SPMV])
+        e0.record()
+        for _ in range(steps):
+            its, _ = step()
+        e1.record()
+        torch.cuda.synchronize()
+        live = B.gs_profile_end(ctx)
+        sec = e0.elapsed_time(e1) / 1e3
+        apply_line, spmv_line = kernel_lines(B, ctx, dev, clk, "ff", B.GS_PREC_FP32, 1, N, n, nnzb, nd, mp, live,
+                                             alone)
+        dominant = apply_line if live[1][B.GS_K_MAS_APPLY_L0] >= live[1][B.GS_K_SPMV] else spmv_line
+        out = {"workload": "tet cube 100^3 (1M vertices, E=1e6) + 2000 affine bodies + 500k contact pairs, "
+                           "two-level ABD assembly, 3-level MAS N=32 with FP32 inverses, forward PCG + adjoint "
+                           "(L = ||x - x_t||^2) to 1e-6, dL/dH on the pattern, one stream",
+               "value": steps / sec, "unit": "differentiated solves/s (forward + adjoint)",
+               "ms_per_step": sec / steps * 1e3, "steps": steps, "pcg_iterations": {"forward": its[0],
+                                                                                 "adjoint": its[1]},
+               "reduced_rows": n, "stored_blocks": nnzb, "input_triplets": n_inputs,
+               "input_generation_s": t_gen, "roofline": dominant,
+               "kernels": {"mas_apply_l0": apply_line, "spmv": spmv_line},
+               "phase_ms_one_step": {B.K_NAMES[k]: float(alone[1][k]) for k in range(B.GS_K_COUNT)}}
+    finally:
+        B.gs_destroy(ctx)
+    if not args.no_cpu_baseline:
+        try:
+            env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                       CUDA_VISIBLE_DEVICES="")
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                                json.dumps({"kind": "abd", "n": 32})], env=env, capture_output=True, text=True,
+                               timeout=1800)
+            res = json.loads(r.stdout.strip().splitlines()[-1])
+            # per-unit rates of the sample applied to the full scene: assembly per
+            # input triplet, build per reduced row, PCG per stored block and iteration
+            t_ga = res["t_ga"] * n_inputs / res["inputs"]
+            t_pa = res["t_pa"] * n / res["rows"]
+            per_it = (res["t_fwd"] + res["t_adj"]) / sum(res["iters"]) * nnzb / res["stored"]
+            tot = t_ga + t_pa + per_it * sum(its)
+            out["cpu_baseline"] = {
+                "value": 1.0 / tot, "unit": "differentiated solves/s (forward + adjoint)", "cores": 1,
+                "kind": "oracle",
+                "sample": (f"the FP64 numpy/scipy oracle's complete differentiated solve on one host core "
+                           f"({res['host']['cpu_model']}) of the same recipe at 32^3 vertices "
+                           f"({res['rows']} reduced rows, {res['stored']} stored blocks): assembly "
+                           f"{res['t_ga']:.2f} s, MAS build {res['t_pa']:.2f} s, forward + adjoint PCG "
+                           f"{res['t_fwd'] + res['t_adj']:.2f} s ({res['iters']} iterations); scaled to this scene "
+                           f"per input triplet, reduced row and stored block x iteration (the GPU's counts)"),
+                "sample_rate": 1.0 / (res["t_ga"] + res["t_pa"] + res["t_fwd"] + res["t_adj"]),
                 "host": res["host"]}
         except Exception as e:  # noqa: BLE001
             out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
@@ -691,6 +879,8 @@ def main():
             oracle_full_plain16(spec)
         elif spec.get("kind") == "elastic":
             oracle_elastic_sample(spec)
+        elif spec.get("kind") == "abd":
+            oracle_abd_sample(spec)
         else:
             oracle_sample(spec)
         return
@@ -1244,6 +1434,14 @@ def main():
         except B.GsError as e:
             newton_f = {"error": str(e)[:300]}
 
+    # the differentiation form on the coupled FEM + affine-body scene
+    abd_f = None
+    if args.abd:
+        try:
+            abd_f = abd_form(args, B, dev, clk)
+        except B.GsError as e:
+            abd_f = {"error": str(e)[:300]}
+
     # roofline of the dominant kernel class
     apply_line, spmv_line = kernel_lines(B, ctx, dev, clk, args.spmv, prec, args.nrhs, N, V, nnzb, ndom, mp,
                                          (launches, kms), (launches_1, ms_1),
@@ -1288,7 +1486,7 @@ def main():
         "launches_one_step": {B.K_NAMES[k]: int(launches_1[k]) for k in range(B.GS_K_COUNT)},
         "e2e": e2e,
         "forms": {"mixed_precision": mixed, "batched": batched, "precision_cloth": cloth, "plain16": plain16,
-                  "partitions": partitions, "newton": newton_f},
+                  "partitions": partitions, "newton": newton_f, "differentiation_abd": abd_f},
         "clocks": clk,
         "gpu_launches": mine,
         "libprim_calls": int(launches[B.GS_K_LIBPRIM]),

@@ -333,9 +333,16 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 #define GS_TUNE_BF16_TC 4         /* BF16 level-0 apply on the tensor cores (1, default) or on FP32 cores (0);
                                      the tensor-core form needs 3N a multiple of 16 (N = 16, 32) and nrhs <= 8 */
 #define GS_TUNE_F64_TC 5          /* FP64 MAS apply on the BF16 tensor cores by exact digit splitting (FP64
-                                     accuracy): 1 (default) one CTA per domain, 2 one persistent warp-
-                                     specialised CTA per SM for level 0; 0 on the FP64 cores.  Needs 3N a
-                                     multiple of 16 and nrhs <= 8 */
+                                     accuracy): 1 (default) from 7 BF16 digit matrices per inverse (3.5x
+                                     the bytes of the packed FP64 lower triangle), one CTA per domain; 2 the
+                                     same digits, one persistent warp-specialised CTA per SM for level 0; 3
+                                     from each symmetric inverse's block lower triangle, scaled
+                                     symmetrically and stored as 8 base-128 digit bytes per entry (1.07x),
+                                     expanded to BF16 in shared memory (fewer bytes, more instructions); 0
+                                     on the FP64 cores.  The digit storage is made when a preconditioner is built or
+                                     refreshed, for the value set then; applying it with a value whose
+                                     storage was not made uses the FP64 cores.  Needs N = 16 or 32 and
+                                     nrhs <= 8 */
 #define GS_TUNE_SPMV_WINDOW 6     /* row order of the row SpMVs: longest rows first within windows of this
                                      many consecutive rows (256..65536, a power of 2; default 1024), so that
                                      the rows in flight stay neighbours and their gathers hit L2; 0: over

@@ -16,8 +16,12 @@ The shapes and the kernels they steer:
   * GS_TUNE_BATCH_CHUNK  vector entries per work item of the batched PCG reductions;
   * GS_TUNE_BF16_TC      BF16 level-0 apply on the tensor cores or on the FP32 cores;
   * GS_TUNE_F64_TC       FP64 apply on the BF16 tensor cores (exact digit
-                         splitting; one CTA per domain or one persistent CTA
-                         per SM) or on the FP64 cores;
+                         splitting) or on the FP64 cores.  The digit storage is
+                         made when the preconditioner is built, so the sweep
+                         stays within the storage built: the symmetric digit
+                         bytes (3) or the FP64 cores, or the BF16 digit
+                         matrices (one CTA per domain 1, persistent 2) or the
+                         FP64 cores;
   * GS_TUNE_SPMV_WS      one thread group per row, or a persistent grid whose
                          warps steal the next rows;
   * GS_TUNE_SPMV_FF_RHS  right-hand sides per thread of the float-float SpMV
@@ -120,7 +124,9 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
         out[NAMES[B.GS_TUNE_SPMV_FF_RHS]] = sweep(ctx, B.GS_TUNE_SPMV_FF_RHS, B.GS_K_SPMV, spmv, reps)
     apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
     if fp64:
-        out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps)
+        built = B.gs_tune_get(ctx, B.GS_TUNE_F64_TC)  # the value `mas` was built with
+        cands = (3, 0) if built == 3 else (1, 2, 0) if built in (1, 2) else (0,)
+        out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps, cands)
     if not fp64 or B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 0:  # the FP64-core kernel's shape
         out[NAMES[B.GS_TUNE_APPLY_RHS]] = sweep(ctx, B.GS_TUNE_APPLY_RHS, B.GS_K_MAS_APPLY_L0, apply, reps)
     if bf16:

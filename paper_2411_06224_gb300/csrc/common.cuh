@@ -163,6 +163,14 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
                         int64_t lstride, double* z, const int* skip = nullptr);
 int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride,
                         const int* skip = nullptr);
+// The same product from the block lower triangles of the symmetric inverses
+// as digit bytes (GS_TUNE_F64_TC = 3, N = 16 or 32); mas_apply_f64sym.cu.
+bool f64sym_shape_ok(int N);
+int f64sym_prepare(gs_ctx ctx, gs_mas mas);
+int f64sym_level0_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
+                         int64_t lstride, double* z, const int* skip);
+int f64sym_coarse_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride,
+                         const int* skip);
 // y = A x (row or SRBK variant) and z = M^{-1} r, with the same skip word
 int spmv_launch_skip(gs_ctx ctx, gs_mat m, const double* x, double* y, int nrhs, int variant, const int* skip);
 int mas_apply_launch_skip(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrhs, double* rl, double* zl,
@@ -225,6 +233,10 @@ struct gs_mas_s {
   std::vector<void*> dig64;        // FP64 precision: per level, the inverses as 7 BF16 digit matrices per domain
   std::vector<int32_t*> dig64_exp; // FP64 precision: per level, their row exponents
   void** d_dig_tab = nullptr;      // device table: digit pointers [0..7], exponent pointers [8..15]
+  std::vector<void*> dig8;         // FP64 precision, GS_TUNE_F64_TC = 3: per level, the inverses' block lower
+                                   // triangles as 8 base-128 digit bytes per entry
+  std::vector<int32_t*> dig8_scale;  // their symmetric row scales c_i
+  void** d_sym_tab = nullptr;      // device table: digit-byte pointers [0..7], scale pointers [8..15]
   std::vector<int64_t> vec_off;    // per level l >= 1: offset (in items) into the multilevel vector
   int64_t vec_items = 0;           // total items of levels >= 1
   void** d_inv_tab = nullptr;      // device table: inverse pointer per level (FP64 or FP32)

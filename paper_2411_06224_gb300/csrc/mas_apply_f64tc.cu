@@ -34,6 +34,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fp64split.cuh"
 #include "umma.cuh"
 
 namespace gs {
@@ -63,54 +64,9 @@ __host__ inline size_t smem_bytes(int ld) {
 }
 
 // T 2^e as the nearest double (ties to even), T = hi 2^32 + lo with
-// |hi|, |lo| < 2^49, in integer arithmetic only: the 128-bit magnitude is
-// normalised, rounded to 53 bits and packed with its exponent.  Results
-// below the normal range flush to zero.
+// |hi|, |lo| < 2^49.
 __device__ __forceinline__ double scaled_to_double(long long hi, long long lo, int e) {
-  __int128 T = ((__int128)hi << 32) + (__int128)lo;
-  if (T == 0) return 0.0;
-  const unsigned long long sign = T < 0 ? 0x8000000000000000ULL : 0ULL;
-  unsigned __int128 M = (unsigned __int128)(T < 0 ? -T : T);
-  const unsigned long long top = (unsigned long long)(M >> 64);
-  const int lz = top ? __clzll(top) : 64 + __clzll((unsigned long long)M);
-  M <<= lz;  // leading one at bit 127
-  unsigned long long mant = (unsigned long long)(M >> 75);  // 53 bits
-  const unsigned __int128 rest = M & ((((unsigned __int128)1) << 75) - 1);
-  const unsigned __int128 half = ((unsigned __int128)1) << 74;
-  int E = 127 - lz + e;  // value = 1.f 2^E
-  if (rest > half || (rest == half && (mant & 1))) {
-    if (++mant == (1ULL << 53)) {
-      mant >>= 1;
-      ++E;
-    }
-  }
-  if (E < -1022) return 0.0;
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
-}
-
-// Biased exponent field of a double (0 for zero / subnormal).
-__device__ __forceinline__ int biased_exp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
-
-// rint(v * 2^(56 - b)) for |v| < 2^(b-1), in integer arithmetic (round half
-// to even), so no FP64 instruction is spent on the split.
-__device__ __forceinline__ long long scaled_rint(double v, int b) {
-  const long long bits = __double_as_longlong(v);
-  const int eb = (int)((bits >> 52) & 0x7FF);
-  if (eb == 0) return 0;  // zero or subnormal: far below the column scale
-  const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;  // 53 bits
-  const int sh = eb - 1075 + 56 - b;  // value = mant 2^(eb - 1075); times 2^(56 - b)
-  long long q;
-  if (sh >= 0) {
-    q = mant << sh;  // sh <= 2 by the bound on |v|
-  } else {
-    const int s = -sh;
-    if (s > 54) return 0;
-    const long long half = 1LL << (s - 1);
-    q = mant >> s;
-    const long long rem = mant & ((1LL << s) - 1);
-    q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
-  }
-  return bits < 0 ? -q : q;
+  return combine_to_double(hi, lo, 32, e);
 }
 
 // Balanced base-256 digits of x (|x| < 2^55): x = sum_p d[p] 256^(6-p), d[0] the
@@ -155,7 +111,7 @@ __global__ void k_split_inverse(const double* __restrict__ inv, int ld, __nv_bfl
 //   z = level-0 product + prolongated coarse results, written per node;
 // kCoarse = true: one coarse-level domain per CTA (job tables), r and z are the
 //   level's contiguous multilevel vectors rl, zl.
-template <bool kCoarse, int kS>
+template <bool kCoarse, int kS, int LD>
 __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* const* __restrict__ dig_tab,
                                                            const int32_t* const* __restrict__ exp_tab,
                                                            const int32_t* __restrict__ job_level,
@@ -168,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   using namespace umma;
   if (skip && *skip) return;  // whole CTA, before any barrier or TMEM use
   extern __shared__ unsigned char smem_raw[];
-  const int ld = 3 * N;
+  constexpr int ld = LD;  // 3 N
   const uint32_t sbytes = slot_bytes(ld), bb = b_bytes(ld);
   const uint32_t dig_bytes = (uint32_t)ld * ld * 2;
   unsigned char* ring = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -236,12 +192,8 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
     if (e >= 8 * ld) break;
     const int k = e / ld, j = e - k * ld;
     const long long y = scaled_rint(rv[m], sexp[k] - 1021);  // 0 for zero entries
-    int dg[kDigits];
-    digits(y, dg);
-    unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)  // column n = 8 q + k; q = 7: the missing 8th digit, zero
-      *(__nv_bfloat16*)(col + q * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
+    // column n = 8 q + k; q = 7: the missing 8th digit, zero
+    write_digits256_bf16(y, sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16);
   }
   fence_proxy_async();
   __syncthreads();
@@ -319,10 +271,17 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
       mbar_arrive(done);
     }
   }
-  __syncwarp();
-  bool ok = mbar_wait(done, 0);
-  if (!ok) atomicOr(flags, kErrTimeout);
-  ok = __all_sync(0xffffffffu, ok) && !*sfail;
+  // warp 0 waits for the MMAs; the other warps wait at the barrier, where they
+  // take no issue slots
+  if (warp == 0) {
+    __syncwarp();
+    bool fin = mbar_wait(done, 0);
+    if (!fin) atomicOr(flags, kErrTimeout);
+    fin = __all_sync(0xffffffffu, fin);
+    if (lane == 0 && !fin) *sfail = 1;
+  }
+  __syncthreads();
+  const bool ok = !*sfail;
   fence_after_sync();
   if (ok && warp * 32 < ld) {
     const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
@@ -560,12 +519,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
         if (e >= 8 * ld) break;
         const int k = e / ld, j = e - k * ld;
         const long long y = scaled_rint(rv[m], se[k] - 1021);
-        int dg[kDigits];
-        digits(y, dg);
-        unsigned char* col = sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)  // column n = 8 q + k; q = 7: the missing 8th digit, zero
-          *(__nv_bfloat16*)(col + q * 128) = __int2bfloat16_rn(q < kDigits ? dg[q] : 0);
+        write_digits256_bf16(y, sB + (j >> 3) * 1024 + (j & 7) * 2 + k * 16);
       }
       fence_proxy_async();
       named_sync(1, 64);
@@ -656,14 +610,22 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
 
 }  // namespace f64tc
 
+// GS_TUNE_F64_TC: 1 / 2 stream the BF16 digit matrices of this file, 3 the
+// symmetric digit bytes of mas_apply_f64sym.cu; the storage is made when the
+// preconditioner is built for the value set then.
 bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs) {
-  return mas->precision == GS_PREC_FP64 && !mas->dig64.empty() && nrhs >= 1 && nrhs <= 8 &&
-         ctx->tune[GS_TUNE_F64_TC] != 0;
+  if (mas->precision != GS_PREC_FP64 || nrhs < 1 || nrhs > 8) return false;
+  const int t = ctx->tune[GS_TUNE_F64_TC];
+  if (t == 3) return !mas->dig8.empty();
+  return (t == 1 || t == 2) && !mas->dig64.empty();
 }
 
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas) {
   const int ld = 3 * mas->N;
-  if (mas->precision != GS_PREC_FP64 || ld % 16 != 0 || ld > f64tc::kM || !mas->dig64.empty()) return GS_OK;
+  const int t = ctx->tune[GS_TUNE_F64_TC];
+  if (mas->precision != GS_PREC_FP64 || t == 0) return GS_OK;
+  if (t == 3) return f64sym_shape_ok(mas->N) ? f64sym_prepare(ctx, mas) : GS_OK;
+  if (ld % 16 != 0 || ld > f64tc::kM || !mas->dig64.empty()) return GS_OK;
   for (int l = 0; l < mas->L; ++l) {  // every level: level 0 and the coarse levels
     const int64_t n_dom = mas->n_domains[l];
     void* dg = nullptr;
@@ -696,6 +658,7 @@ static f64tc::Levels f64tc_levels(gs_mas mas) {
 int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64_t stride, const double* zl,
                         int64_t lstride, double* z, const int* skip) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
+  if (ctx->tune[GS_TUNE_F64_TC] == 3) return f64sym_level0_launch(ctx, mas, nrhs, r, stride, zl, lstride, z, skip);
   if (mas->n_domains[0] == 0) return GS_OK;
   if (ctx->tune[GS_TUNE_F64_TC] == 2) {  // persistent, warp-specialised: one CTA per SM
     const size_t psmem = f64tc::psmem_bytes(3 * mas->N);
@@ -711,11 +674,19 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
   const size_t smem = f64tc::smem_bytes<f64tc::kSlots>(3 * mas->N);
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false, f64tc::kSlots>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  f64tc::k_level0_f64tc<false, f64tc::kSlots><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>(
-      tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,
-      ctx->d_flags, skip);
+  // 3 N = 96 or 48 (the digit storage is made only for N = 32 and 16)
+#define GS_F64TC_L0(LD)                                                                                     \
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false, f64tc::kSlots, LD>,                             \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                    \
+  f64tc::k_level0_f64tc<false, f64tc::kSlots, LD><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>( \
+      tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,   \
+      ctx->d_flags, skip)
+  if (mas->N == 32) {
+    GS_F64TC_L0(96);
+  } else {
+    GS_F64TC_L0(48);
+  }
+#undef GS_F64TC_L0
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -723,17 +694,25 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
 int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, double* zl, int64_t lstride,
                         const int* skip) {
   GS_CHECK(level0_f64tc_usable(ctx, mas, nrhs), GS_ERR_UNSUPPORTED, "FP64 tensor-core apply: not available");
+  if (ctx->tune[GS_TUNE_F64_TC] == 3) return f64sym_coarse_launch(ctx, mas, nrhs, rl, zl, lstride, skip);
   if (mas->n_coarse_jobs == 0) return GS_OK;
   // a few hundred coarse domains at most: a deeper ring per CTA shortens the
   // chain of copy latencies that bounds this small launch
   const size_t smem = f64tc::smem_bytes<f64tc::kSlotsCoarse>(3 * mas->N);
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
-  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(
-      tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,
-      f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags, skip);
+#define GS_F64TC_CO(LD)                                                                                          \
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD>,                             \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                         \
+  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>( \
+      tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,             \
+      f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags, skip)
+  if (mas->N == 32) {
+    GS_F64TC_CO(96);
+  } else {
+    GS_F64TC_CO(48);
+  }
+#undef GS_F64TC_CO
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

@@ -553,9 +553,12 @@ static void mas_release_numeric(gs_mas mas) {
   for (auto p : mas->inv16) c->release(p);
   for (auto p : mas->dig64) c->release(p);
   for (auto p : mas->dig64_exp) c->release(p);
+  for (auto p : mas->dig8) c->release(p);
+  for (auto p : mas->dig8_scale) c->release(p);
   c->release(mas->inv32p);
   c->release(mas->inv16_tc);
   c->release(mas->d_dig_tab);
+  c->release(mas->d_sym_tab);
   c->release(mas->d_inv_tab);
   c->release(mas->d_coarse_jobs);
   c->release(mas->d_inv32_tab);
@@ -564,6 +567,9 @@ static void mas_release_numeric(gs_mas mas) {
   mas->inv16.clear();
   mas->dig64.clear();
   mas->dig64_exp.clear();
+  mas->dig8.clear();
+  mas->dig8_scale.clear();
+  mas->d_sym_tab = nullptr;
   mas->inv32p = nullptr;
   mas->inv16_tc = nullptr;
   mas->d_dig_tab = nullptr;
@@ -594,6 +600,9 @@ int gs_mas_destroy(gs_mas mas) {
   for (auto p : mas->dig64) c->release(p);
   for (auto p : mas->dig64_exp) c->release(p);
   c->release(mas->d_dig_tab);
+  for (auto p : mas->dig8) c->release(p);
+  for (auto p : mas->dig8_scale) c->release(p);
+  c->release(mas->d_sym_tab);
   c->release(mas->remap0);
   c->release(mas->d_inv_tab);
   c->release(mas->d_coarse_jobs);

@@ -26,12 +26,13 @@ inputs; none of it is solver arithmetic.
 """
 
 from dataclasses import dataclass
+from types import SimpleNamespace
 
 import numpy as np
 
 from .hessians import contact_blocks, near_pairs
-from .mesh import adjacency_csr
-from .workloads import make_tet_system
+from .mesh import adjacency_csr, unique_sorted
+from .workloads import make_tet_system, tet_geometry
 
 
 @dataclass
@@ -49,6 +50,8 @@ class AbdScene:
     adj: np.ndarray
     contacts: np.ndarray  # int32 (P, 2) contact couplings on reduced rows
     params: dict
+    fem_x: np.ndarray = None     # with fem_blocks=False: the FEM part's deformed positions,
+    fem_tets: np.ndarray = None  # and its tets (its Hessian blocks are left to the caller)
 
     @property
     def n_red(self):
@@ -75,9 +78,18 @@ def _orthogonality_hessian(A, kv):
 
 
 def make_abd_scene(n=100, n_bodies=2000, n_contacts=500_000, E=1e6, rho=1000.0, dt=0.01, kappa=1e11,
-                   size=0.02, seed=1005):
+                   size=0.02, seed=1005, fem_blocks=True):
+    """The scene of the recipe above.  fem_blocks=False leaves out the FEM
+    part's element and mass blocks (same geometry, same draws for the rest)
+    and returns its deformed positions and tets instead, for a caller that
+    computes those blocks itself."""
     rng = np.random.default_rng(seed)
-    fem = make_tet_system(n, E=E, rho=rho, dt=dt, n_contacts=0, seed=seed)
+    if fem_blocks:
+        fem = make_tet_system(n, E=E, rho=rho, dt=dt, n_contacts=0, seed=seed)
+    else:
+        X_, x_, tets_, ptr_, adj_ = tet_geometry(n, seed=seed)
+        fem = SimpleNamespace(n_vertices=X_.shape[0], X=X_, x=x_, tets=tets_, adj_ptr=ptr_, adj=adj_,
+                              rows=np.zeros(0, np.int32), cols=np.zeros(0, np.int32), blocks=np.zeros((0, 3, 3)))
     V = fem.n_vertices
     h = 1.0 / (n - 1)
     g = int(np.ceil(np.sqrt(n_bodies)))
@@ -151,7 +163,10 @@ def make_abd_scene(n=100, n_bodies=2000, n_contacts=500_000, E=1e6, rho=1000.0, 
             x = ra + np.where(pairs[:, 0] >= V, a, 0)
             y = rb + np.where(pairs[:, 1] >= V, c, 0)
             cpl.append(np.stack([np.minimum(x, y), np.maximum(x, y)], -1))
-    cpl = np.unique(np.concatenate(cpl), axis=0)
+    cpl = np.concatenate(cpl).astype(np.int64)
+    nr = V + 4 * n_bodies
+    key = unique_sorted(cpl[:, 0] * nr + cpl[:, 1])  # distinct pairs in (first, second) order
+    cpl = np.stack([key // nr, key % nr], -1)
     cpl = cpl[cpl[:, 0] != cpl[:, 1]].astype(np.int32)
     return AbdScene(
         n_nodes=n_nodes, n_fem=V, n_bodies=n_bodies, body_of_node=body_of_node, xbar=xbar,
@@ -159,4 +174,5 @@ def make_abd_scene(n=100, n_bodies=2000, n_contacts=500_000, E=1e6, rho=1000.0, 
         X=Xr, adj_ptr=ptr, adj=adj, contacts=cpl,
         params=dict(n=n, n_bodies=n_bodies, n_contacts=n_contacts, E=E, rho=rho, dt=dt, kappa=kappa, size=size,
                     seed=seed),
+        fem_x=None if fem_blocks else fem.x, fem_tets=None if fem_blocks else fem.tets,
     )

@@ -41,13 +41,22 @@ def tet_cube(n, rng=None, jitter=0.05):
     return X, tets.astype(np.int32)
 
 
+def unique_sorted(a):
+    """Sorted distinct values of a 1-D integer array (a sort and a neighbour
+    test: some numpy releases take a far slower hashing path in np.unique)."""
+    s = np.sort(np.asarray(a).ravel())
+    if s.size == 0:
+        return s
+    return s[np.concatenate([[True], s[1:] != s[:-1]])]
+
+
 def tet_edges(tets):
     """Unique undirected vertex pairs (a < b) of a tet mesh, sorted, (E, 2) int64."""
     t = tets.astype(np.int64)
     pairs = np.concatenate([t[:, [a, b]] for a in range(4) for b in range(a + 1, 4)])
     pairs.sort(axis=1)
     V = int(t.max()) + 1 if t.size else 1
-    key = np.unique(pairs[:, 0] * V + pairs[:, 1])
+    key = unique_sorted(pairs[:, 0] * V + pairs[:, 1])
     return np.stack([key // V, key % V], -1)
 
 
@@ -58,7 +67,7 @@ def adjacency_csr(n_vertices, edges):
     dst = np.concatenate([e[:, 1], e[:, 0]])
     keep = src != dst
     src, dst = src[keep], dst[keep]
-    key = np.unique(src * n_vertices + dst)
+    key = unique_sorted(src * n_vertices + dst)
     src, dst = key // n_vertices, key % n_vertices
     ptr = np.zeros(n_vertices + 1, dtype=np.int64)
     np.add.at(ptr, src + 1, 1)

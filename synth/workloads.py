@@ -84,6 +84,19 @@ def _geometry(n, nu, rho, dt, n_contacts, contact_mode, k_range, seed):
     return _Geometry(n, X, tets, r_e, c_e, b_e, mass, pairs, ctrip, ptr, adj, seed + 7919)
 
 
+def tet_geometry(n, seed=1000):
+    """Rest positions X, deformed positions x, tets and the mesh graph of the n^3
+    cube of the recipe above, from the same draws as make_tet_systems (no
+    Hessian blocks): the inputs of a device element-Hessian kernel."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n - 1)
+    X, tets = tet_cube(n, rng, jitter=0.05)
+    G = rng.uniform(-0.1, 0.1, (3, 3))
+    x = X @ (np.eye(3) + G).T + rng.normal(0.0, 0.02 * h, X.shape)
+    ptr, adj = adjacency_csr(X.shape[0], tet_edges(tets))
+    return X, x, tets.astype(np.int32), ptr, adj
+
+
 def _system(g, E, params):
     rows = np.concatenate([g.unit_rows, g.mass[0], g.contact_trip[0]]).astype(np.int32)
     cols = np.concatenate([g.unit_cols, g.mass[1], g.contact_trip[1]]).astype(np.int32)

@@ -52,7 +52,7 @@ def build(B, ctx, s, N=16, L=3, node_off=None):
 def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
-                       (B.GS_TUNE_F64_TC, 3), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
+                       (B.GS_TUNE_F64_TC, 4), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
                        (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_SPMV_WS, 2), (B.GS_TUNE_SPMV_FF_RHS, 3),
                        (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
@@ -123,7 +123,7 @@ def test_every_shape_gives_the_oracle_result(B, ctx):
         B.gs_tune_set(ctx, B.GS_TUNE_APPLY_RHS, rpt)
         B.gs_mas_apply(ctx, M, xd, y, nrhs=nrhs)
         zs[rpt] = y.cpu().numpy()
-    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 1)
+    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 1)  # the digit storage this preconditioner was built with
     B.gs_mas_apply(ctx, M, xd, y, nrhs=nrhs)
     zs["tensor_cores"] = y.cpu().numpy()
     z0 = np.stack([Mo(v) for v in x])

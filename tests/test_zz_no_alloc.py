@@ -58,7 +58,8 @@ def _noalloc(B, ctx, mas, r, z, nrhs):
 # to a few FP32 roundings (their coarse levels read restricted vectors whose
 # atomic sums may round differently from call to call).
 _PATHS = [
-    (0, 1, 4, 1e-12),   # FP64 accuracy on the tensor cores, every level
+    (0, 3, 4, 1e-12),   # FP64 accuracy on the tensor cores from symmetric digit bytes, every level
+    (0, 1, 4, 1e-12),   # FP64 accuracy on the tensor cores from BF16 digit matrices, every level
     (0, 0, 4, 1e-12),   # FP64 cores
     (0, 1, 12, 1e-12),  # more than 8 RHS: FP64 cores
     (1, 1, 4, 1e-5),    # FP32 inverses
