@@ -22,7 +22,13 @@ It restates, in numpy, what the paper's hot path computes:
   stored blocks, ``pcg.SymmetricMatrix`` as a scipy BSR operator.
 * ``adjoint``   -- gradients of a loss through x = H^-1 b.
 * ``strain_limit`` -- the cubic strain-limiting energy of Sec. 4 and its
-  analytic eigensystem (input generation).
+  analytic eigensystem.
+* ``elastic``   -- stable Neo-Hookean element Hessians (PSD-projected, pulled
+  back to the node blocks) and lumped masses of a tet mesh (Sec. 3.1).
+* ``newton``    -- Newton's method on the implicit-Euler incremental potential
+  (Fig. framework; supplement Eq. 1).
+* ``cloth``     -- the stiff-cloth element Hessians: membrane with the cubic
+  strain limit of Sec. 4, hinge bending, lumped masses.
 
 Every floating-point quantity is float64.
 """
