@@ -698,6 +698,93 @@ def abd_form(args, B, dev, clk):
     return out
 
 
+# FP64 operations per element of the cloth kernels, counted from their source
+# (FMA = 2; square roots and divisions as 1): triangle = F (18 FMA), two
+# directions (norm, coefficients, 9 entries of c_f f f^T + c_i I: 36 each),
+# the shear terms (27 entries, 3 each) and 6 blocks (4 weight products, 9
+# entries of 4 weighted terms and the area scale: 8 each); hinge = edge
+# vectors, normals, norms and projections (65), gradients (12 entries, 3 each)
+# and 10 blocks of 9 products of 2
+CLOTH_FLOP_TRI = 36 + 2 * 36 + 27 * 3 + 6 * (4 + 9 * 8)
+CLOTH_FLOP_HINGE = 65 + 12 * 3 + 10 * 9 * 2
+
+
+def cloth_element_line(args, B, dev, stream, clk):
+    """Device cloth element Hessians (gs_cloth_triplets) on the bench's sheet:
+    elements per second, the FP64 roofline of the launch sequence, and the
+    oracle's per-element rate on a 48 x 48 sample of the same recipe."""
+    import numpy as np
+    import torch
+
+    from synth.cloth import hinges, sheet
+
+    n = args.cloth
+    X, tris = sheet(n)
+    hg = hinges(tris)
+    rng = np.random.default_rng(1003)
+    h = 1.0 / (n - 1)
+    sh = rng.uniform(0.0, 0.1)
+    x = X @ np.array([[1.02, sh, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]).T + rng.normal(0.0, 0.01 * h, X.shape)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    ctx = B.gs_create(dev.index or 0, stream)
+    try:
+        c = B.gs_cloth_create(ctx, t(X, torch.float64), t(tris, torch.int32), t(hg, torch.int32), 1e8, 0.05e6, 1e-3,
+                              200.0, 0.01)
+        xd = t(x, torch.float64)
+        nt = B.gs_cloth_info(c)
+        rows = torch.empty(nt, dtype=torch.int32, device=dev)
+        cols = torch.empty(nt, dtype=torch.int32, device=dev)
+        blocks = torch.empty((nt, 3, 3), dtype=torch.float64, device=dev)
+        call = lambda: B.lib().gs_cloth_triplets(ctx, c, ctypes_ptr(xd), ctypes_ptr(rows), ctypes_ptr(cols),
+                                                 ctypes_ptr(blocks))
+        for _ in range(3):
+            call()
+        reps = 10
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        B.gs_cloth_destroy(c)
+    finally:
+        B.gs_destroy(ctx)
+    T, H, V = len(tris), len(hg), X.shape[0]
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    fp64_peak = props.multi_processor_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    flops = CLOTH_FLOP_TRI * T + CLOTH_FLOP_HINGE * H
+    nbytes = T * (3 * 24 + 48 + 8 + 12 + 6 * 80) + H * (4 * 24 + 16 + 8 + 10 * 80) + V * (8 + 80)
+    out = {"workload": f"cloth {n}x{n}: {T} triangles, {H} hinges, {V} vertices -> {nt} triplets",
+           "value": (T + H) / sec, "unit": "elements/s (triangles + hinges)", "ms_per_launch_sequence": sec * 1e3,
+           "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": flops / sec / 1e12 / fp64_peak, "traffic": None, "flops_per_launch": flops,
+                        "bytes_per_launch": nbytes, "hbm_gbs": nbytes / sec / 1e9,
+                        "kernel": "k_cloth_membrane + k_cloth_bending + k_cloth_mass_blocks (FP64)"}}
+    if not args.no_cpu_baseline:
+        from oracle import cloth as ocloth
+
+        Xs, ts = sheet(48)
+        hs = hinges(ts)
+        xs = Xs @ np.array([[1.02, sh, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]).T
+        t0 = time.perf_counter()
+        ocloth.cloth_triplets(Xs, xs, ts, hs, 1e8, 0.05e6, 1e-3, 200.0, 0.01)
+        dt_ = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": (len(ts) + len(hs)) / dt_, "unit": "elements/s (triangles + hinges)",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"oracle.cloth.cloth_triplets on a 48x48 sheet of the same recipe "
+                                         f"({len(ts)} triangles, {len(hs)} hinges), numpy, one process"}
+    return out
+
+
+def ctypes_ptr(tensor):
+    import ctypes
+
+    return ctypes.c_void_p(tensor.data_ptr())
+
+
 def element_probe(args):
     """The Newton form's elastic cube at --element-probe vertices per edge:
     body created (element keys sorted), springs set, Hessian assembled at the
@@ -1281,6 +1368,10 @@ def main():
                 cloth[name] = row
             except B.GsError as e:
                 cloth[name] = {"error": str(e)[:300]}
+        try:
+            cloth["element_hessians"] = cloth_element_line(args, B, dev, stream, clk)
+        except B.GsError as e:
+            cloth["element_hessians"] = {"error": str(e)[:300]}
 
     # the batched form: 64 independent uneven tet cubes (1k-50k vertices, E 1e5-1e9,
     # contacts on 5% of the vertices), one RHS each, solved as one block-diagonal

@@ -448,6 +448,40 @@ int gs_fem_destroy(gs_fem fem);
  * Errors: as gs_build_mas; GS_ERR_INVALID for a matrix of another size. */
 int gs_mas_refresh(gs_ctx ctx, gs_mas mas, gs_mat mat);
 
+/* ---------------------------------------------------------------- stiff cloth
+ * Element Hessians of a triangle sheet on the device (the stiff-cloth
+ * scenes; Sec. 4 for the strain limit): per triangle, with F = sum_a x_a w_a^T
+ * from the in-plane rest edge matrix and a_t = rest area * thickness, the
+ * membrane Hessian a_t (Baraff-Witkin stretching lam (|f_d| - 1)^2 per
+ * direction with its negative eigenvalue clamped, the cubic strain limit
+ * E max(|f_d| - 1, 0)^3 with the analytic PSD Hessian of Eq. Stretch_Hessian,
+ * Gauss-Newton shearing 0.3 lam (f_0 . f_1)^2) pulled back to the vertex
+ * blocks; per interior edge (hinge) the Gauss-Newton bending Hessian
+ * 2 k_b grad(theta) grad(theta)^T of the dihedral angle, k_b = E t^3 / 12
+ * |e_rest|^2 / (A_1 + A_2); lumped masses rho t A / 3 per triangle corner as
+ * m / dt^2 I. */
+typedef struct gs_cloth_s* gs_cloth;
+
+/* X: device double[n_vertices * 3] rest positions (only x and y are used: the
+ * sheet rests in the plane z = 0); tris: device int32[n_tris * 3]; hinges:
+ * device int32[n_hinges * 4] = (e_0, e_1, o_1, o_2), the shared edge and the
+ * opposite vertex of each of its two triangles.  Copied.  Errors:
+ * GS_ERR_INVALID (sizes, E or lam < 0, thickness, rho or dt <= 0, an index out
+ * of range or repeated in a triangle), GS_ERR_NONFINITE (a degenerate rest
+ * triangle or hinge). */
+int gs_cloth_create(gs_ctx ctx, int32_t n_vertices, const double* X, int64_t n_tris, const int32_t* tris,
+                    int64_t n_hinges, const int32_t* hinges, double E, double lam, double thickness, double rho,
+                    double dt, gs_cloth* out);
+/* The Hessian at x (device double[3 n_vertices]) as upper triplets: 6 per
+ * triangle in the pair order (0,0) (0,1) (0,2) (1,1) (1,2) (2,2), then 10 per
+ * hinge in the pair order of (e_0, e_1, o_1, o_2) with a <= b, each at (min,
+ * max) of its two vertices (transposed when the first is the larger), then one
+ * mass block per vertex; rows, cols device int32 (each may be NULL), blocks
+ * device double[9 each] (row-major); gs_cloth_info gives the count. */
+int gs_cloth_triplets(gs_ctx ctx, gs_cloth c, const double* x, int32_t* rows, int32_t* cols, double* blocks);
+int gs_cloth_info(gs_cloth c, int64_t* n_triplets);
+int gs_cloth_destroy(gs_cloth c);
+
 typedef struct gs_newton_opts {
   double tol;            /* stop when max_i |d_i| <= tol * dt (the step's velocity is small) */
   int32_t max_newton;    /* steps at most */

@@ -5,8 +5,8 @@ A triangle sheet with rest positions X (z = 0) and deformed positions x.
 Per triangle (vertices 0, 1, 2) the rest edge matrix Dm (2 x 2, columns
 X_1 - X_0 and X_2 - X_0 in the plane), its area A = |det Dm| / 2 and
 B = Dm^-1 give F = sum_a x_a w_a^T (3 x 2) with w_a = row a - 1 of B for
-a >= 1 and w_0 = -(w_1 + w_2); f_0, f_1 are the columns of F and vec(F) =
-[f_0; f_1].  With a_t = A * thickness the membrane energy is
+a >= 1 and w_0 = -(w_1 + w_2), evaluated from the edges (x_1 - x_0) and
+(x_2 - x_0); f_0, f_1 are the columns of F and vec(F) = [f_0; f_1].  With a_t = A * thickness the membrane energy is
 
   stretching     lam a_t sum_d (|f_d| - 1)^2,
   strain limit   E a_t sum_d max(|f_d| - 1, 0)^3            (Sec. 4, Eq. memb_u),
@@ -64,9 +64,14 @@ def rest_data(X, tris):
 
 
 def deformation(x, tris, w):
-    """F (T, 3, 2) = sum_a x_a w_a^T."""
+    """F (T, 3, 2) = sum_a x_a w_a^T, evaluated from the edge vectors as
+    (x_1 - x_0) w_1^T + (x_2 - x_0) w_2^T (the same value, as w_0 = -(w_1 + w_2),
+    without the cancellation of absolute coordinates against 1/h weights)."""
     x = np.asarray(x, dtype=np.float64)
-    return np.einsum("tax,taj->txj", x[np.asarray(tris)], w)
+    t = np.asarray(tris)
+    e1 = x[t[:, 1]] - x[t[:, 0]]
+    e2 = x[t[:, 2]] - x[t[:, 0]]
+    return e1[:, :, None] * w[:, 1, None, :] + e2[:, :, None] * w[:, 2, None, :]
 
 
 def membrane_energy(F, a_t, lam, E):

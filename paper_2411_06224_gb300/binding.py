@@ -107,6 +107,10 @@ EXPORTS = [
     "gs_fem_destroy",
     "gs_mas_refresh",
     "gs_fem_newton",
+    "gs_cloth_create",
+    "gs_cloth_triplets",
+    "gs_cloth_info",
+    "gs_cloth_destroy",
 ]
 
 
@@ -212,6 +216,11 @@ def lib():
             "gs_mas_refresh": (ctypes.c_int, [_P, _P, _P]),
             "gs_fem_newton": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(gs_newton_opts),
                                              ctypes.POINTER(gs_newton_stats), _P]),
+            "gs_cloth_create": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _I64, _P, _D, _D, _D, _D, _D,
+                                               ctypes.POINTER(_P)]),
+            "gs_cloth_triplets": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+            "gs_cloth_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+            "gs_cloth_destroy": (ctypes.c_int, [_P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -606,6 +615,38 @@ def gs_fem_triplets(ctx, fem, x, n_entries):
                                  _dev(cols, torch.int32, "cols"), _dev(blocks, torch.float64, "blocks")),
            "gs_fem_triplets")
     return rows, cols, blocks
+
+
+def gs_cloth_create(ctx, X, tris, hinges, E, lam, thickness, rho, dt):
+    """X (V, 3) float64, tris (T, 3) int32, hinges (H, 4) int32 CUDA tensors (copied)."""
+    h = _P()
+    _check(lib().gs_cloth_create(ctx, X.shape[0], _dev(X, torch.float64, "X"), tris.shape[0],
+                                 _dev(tris, torch.int32, "tris"), hinges.shape[0], _dev(hinges, torch.int32, "hinges"),
+                                 E, lam, thickness, rho, dt, ctypes.byref(h)), "gs_cloth_create")
+    return h
+
+
+def gs_cloth_info(c):
+    """Number of triplets gs_cloth_triplets writes."""
+    n = _I64()
+    _check(lib().gs_cloth_info(c, ctypes.byref(n)), "gs_cloth_info")
+    return n.value
+
+
+def gs_cloth_triplets(ctx, c, x):
+    """(rows, cols, blocks (n, 3, 3)) CUDA tensors of the cloth Hessian at x ((V, 3) float64)."""
+    n = gs_cloth_info(c)
+    rows = torch.empty(n, dtype=torch.int32, device="cuda")
+    cols = torch.empty(n, dtype=torch.int32, device="cuda")
+    blocks = torch.empty((n, 3, 3), dtype=torch.float64, device="cuda")
+    _check(lib().gs_cloth_triplets(ctx, c, _dev(x, torch.float64, "x"), _dev(rows, torch.int32, "rows"),
+                                   _dev(cols, torch.int32, "cols"), _dev(blocks, torch.float64, "blocks")),
+           "gs_cloth_triplets")
+    return rows, cols, blocks
+
+
+def gs_cloth_destroy(c):
+    _check(lib().gs_cloth_destroy(c), "gs_cloth_destroy")
 
 
 def gs_fem_assemble(ctx, fem, x):
