@@ -448,6 +448,24 @@ int gs_fem_destroy(gs_fem fem);
  * Errors: as gs_build_mas; GS_ERR_INVALID for a matrix of another size. */
 int gs_mas_refresh(gs_ctx ctx, gs_mas mas, gs_mat mat);
 
+/* ---------------------------------------------------------------- assembly primitives
+ * The two device primitives of the hash assembly (Sec. 5.2, Alg.
+ * FastHashReduction), exposed for tests and measurement; gs_assemble and
+ * gs_assemble_abd call them internally.
+ *
+ * gs_prim_sort_pairs: keys_out / vals_out (device uint64[n] / uint32[n])
+ * receive the pairs of keys_in / vals_in sorted by the key bits
+ * [0, end_bit), 1 <= end_bit <= 64, stable (equal keys keep their input
+ * order); a least-significant-digit radix sort with 8-bit digits.  The inputs
+ * are not modified and must not be the outputs.  Uses the context's scratch.
+ * gs_prim_exclusive_scan: out[i] = in[0] + ... + in[i-1] (device int32[n],
+ * n < 2^31, in == out allowed).  Both run on the context's stream and return
+ * without synchronising.  Errors: GS_ERR_INVALID (null pointers, sizes,
+ * end_bit, aliasing), GS_ERR_CUDA. */
+int gs_prim_sort_pairs(gs_ctx ctx, const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                       uint32_t* vals_out, int64_t n, int32_t end_bit);
+int gs_prim_exclusive_scan(gs_ctx ctx, const int32_t* in, int32_t* out, int64_t n);
+
 /* ---------------------------------------------------------------- stiff cloth
  * Element Hessians of a triangle sheet on the device (the stiff-cloth
  * scenes; Sec. 4 for the strain limit): per triangle, with F = sum_a x_a w_a^T

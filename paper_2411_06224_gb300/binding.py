@@ -107,6 +107,8 @@ EXPORTS = [
     "gs_fem_destroy",
     "gs_mas_refresh",
     "gs_fem_newton",
+    "gs_prim_sort_pairs",
+    "gs_prim_exclusive_scan",
     "gs_cloth_create",
     "gs_cloth_triplets",
     "gs_cloth_info",
@@ -216,6 +218,8 @@ def lib():
             "gs_mas_refresh": (ctypes.c_int, [_P, _P, _P]),
             "gs_fem_newton": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(gs_newton_opts),
                                              ctypes.POINTER(gs_newton_stats), _P]),
+            "gs_prim_sort_pairs": (ctypes.c_int, [_P, _P, _P, _P, _P, _I64, _I32]),
+            "gs_prim_exclusive_scan": (ctypes.c_int, [_P, _P, _P, _I64]),
             "gs_cloth_create": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _I64, _P, _D, _D, _D, _D, _D,
                                                ctypes.POINTER(_P)]),
             "gs_cloth_triplets": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -615,6 +619,27 @@ def gs_fem_triplets(ctx, fem, x, n_entries):
                                  _dev(cols, torch.int32, "cols"), _dev(blocks, torch.float64, "blocks")),
            "gs_fem_triplets")
     return rows, cols, blocks
+
+
+def gs_prim_sort_pairs(ctx, keys, vals, end_bit):
+    """Stable radix sort of (keys uint64 as torch.int64, vals int32) CUDA tensors by key bits
+    [0, end_bit); returns new (keys, vals) tensors."""
+    ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+    if keys.numel() and not (keys.dtype == torch.int64 and vals.dtype == torch.int32 and keys.is_cuda and vals.is_cuda
+                             and keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()):
+        raise TypeError("gs_prim_sort_pairs: contiguous CUDA int64 keys and int32 values of one length")
+    _check(lib().gs_prim_sort_pairs(ctx, ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                    ctypes.c_void_p(ko.data_ptr()), ctypes.c_void_p(vo.data_ptr()), keys.numel(),
+                                    end_bit), "gs_prim_sort_pairs")
+    return ko, vo
+
+
+def gs_prim_exclusive_scan(ctx, x, out=None):
+    """Exclusive prefix sum of an int32 CUDA tensor (out may be x)."""
+    out = torch.empty_like(x) if out is None else out
+    _check(lib().gs_prim_exclusive_scan(ctx, _dev(x, torch.int32, "in"), _dev(out, torch.int32, "out"), x.numel()),
+           "gs_prim_exclusive_scan")
+    return out
 
 
 def gs_cloth_create(ctx, X, tris, hinges, E, lam, thickness, rho, dt):

@@ -13,9 +13,9 @@
 // a body's 12 x 12 Hessian (inertia, orthogonality potential) enters as its
 // 16 sub-blocks, Sec. 5.2's ABD-ABD block type, and passes level 2 with
 // weight 1.
-#include <cub/device/device_scan.cuh>
 
 #include "common.cuh"
+#include "sort_scan.cuh"
 
 namespace gs {
 
@@ -145,9 +145,12 @@ extern "C" int gs_assemble_abd(gs_ctx ctx, int32_t n_nodes, int32_t n_fem, int32
                                                       nullptr, nullptr); }
   }
   cudaMemsetAsync(cnt + U, 0, 4, st);
-  cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, off, (int64_t)(U + 1), st);
+  tb = scan_temp_bytes(U + 1);
   if ((s = ctx->alloc(&temp, tb))) goto done;
-  { GS_PROF(ctx, GS_K_LIBPRIM); cub::DeviceScan::ExclusiveSum(temp, tb, cnt, off, (int64_t)(U + 1), st); }
+  {
+    GS_PROF(ctx, GS_K_ASSEMBLE);
+    if ((s = exclusive_scan_i32(st, cnt, off, U + 1, temp, tb))) goto done;
+  }
   if (cudaMemcpyAsync(ctx->h_pinned, off + U, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("gs_assemble_abd: readback failed");

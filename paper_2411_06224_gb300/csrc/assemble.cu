@@ -12,10 +12,9 @@
 // through the sorted index instead of being sorted along (72-byte payloads
 // are read once, in the reduction).
 #include <cub/device/device_reduce.cuh>
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 
 #include "common.cuh"
+#include "sort_scan.cuh"
 #include "primitives.cuh"
 
 namespace gs {
@@ -136,24 +135,20 @@ int reduce_blocks(gs_ctx ctx, int32_t n, const int32_t* rows, const int32_t* col
     O = P + nb;
     const int T = 256;
     { GS_PROF(ctx, GS_K_ASSEMBLE); k_encode_keys<<<ceil_div(nb, T), T, 0, st>>>(rows, cols, nb, n, shift, sentinel, k_in, i_in, ctx->d_flags); }
-    size_t tb = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0, end_bit, st);
+    // radix sort of (key, index) and the exclusive scan of the run flags
+    // (sort_scan.cu: hand-written, stable)
+    const size_t tb = std::max(radix_sort_temp_bytes(nb), scan_temp_bytes(nb));
     void* temp = nullptr;
     if ((s = ctx->scratch_buf(kSlotSortTemp, tb, &temp))) return fail(s);
-    cudaError_t se;
     {
-      GS_PROF(ctx, GS_K_LIBPRIM);
-      se = cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, (int64_t)nb, 0, end_bit, st);
-    }
-    if (se != cudaSuccess) {
-      set_error("radix sort failed");
-      return fail(GS_ERR_CUDA);
+      GS_PROF(ctx, GS_K_ASSEMBLE);
+      if ((s = radix_sort_pairs(st, k_in, k_out, i_in, i_out, nb, end_bit, temp, tb))) return fail(s);
     }
     { GS_PROF(ctx, GS_K_ASSEMBLE); k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(k_out, nb, P); }
-    size_t sb = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, sb, P, O, (int64_t)nb, st);
-    if ((s = ctx->scratch_buf(kSlotSortTemp, std::max(sb, tb), &temp))) return fail(s);
-    { GS_PROF(ctx, GS_K_LIBPRIM); cub::DeviceScan::ExclusiveSum(temp, sb, P, O, (int64_t)nb, st); }
+    {
+      GS_PROF(ctx, GS_K_ASSEMBLE);
+      if ((s = exclusive_scan_i32(st, P, O, nb, temp, tb))) return fail(s);
+    }
     // U = distinct keys, minus the sentinel group if present.
     uint64_t* hk = (uint64_t*)ctx->h_pinned;
     int32_t* ho = (int32_t*)(ctx->h_pinned + 4);
@@ -296,7 +291,7 @@ extern "C" int gs_micro_segment_reduce(gs_ctx ctx, int64_t nb, const uint64_t* k
       goto done;
     k_iota<<<ceil_div(nb, T), T, 0, st>>>(idx, nb);
     int32_t* O = P + nb;
-    cub::DeviceScan::ExclusiveSum(nullptr, tb, P, O, nb, st);
+    tb = scan_temp_bytes(nb);
     if ((s = ctx->alloc(&temp, tb))) goto done;
     // phase 1: flags + scan (then the unique count is read back, untimed);
     // phase 2: zero the U outputs + segmented reduction
@@ -305,7 +300,7 @@ extern "C" int gs_micro_segment_reduce(gs_ctx ctx, int64_t nb, const uint64_t* k
     GS_CUDA(cudaEventCreate(&e3));
     cudaEventRecord(e0, st);
     k_run_flags<<<ceil_div(nb, T), T, 0, st>>>(keys, nb, P);
-    cub::DeviceScan::ExclusiveSum(temp, tb, P, O, nb, st);
+    if ((s = exclusive_scan_i32(st, P, O, nb, temp, tb))) goto done;
     cudaEventRecord(e1, st);
     int32_t* ho = (int32_t*)ctx->h_pinned;
     if (cudaMemcpyAsync(ho, O + nb - 1, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = GS_ERR_CUDA;
