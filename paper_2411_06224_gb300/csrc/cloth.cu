@@ -43,6 +43,9 @@ namespace gs {
 namespace cloth {
 
 constexpr double kShear = 0.3;  // shear stiffness relative to lam
+constexpr int kMemThreads = 128;  // membrane kernel block
+constexpr int kMemStage = 35;     // doubles staged per triangle (34 used; odd stride)
+constexpr int kBendThreads = 128;
 
 // Rest data per triangle: w and a_t; flags a repeated or out-of-range vertex
 // and a degenerate rest triangle.
@@ -138,16 +141,26 @@ __device__ __forceinline__ void emit(int64_t k, int32_t va, int32_t vb, const do
 }
 
 // Membrane blocks: one thread per triangle, 6 blocks at 6 t.
-__global__ void __launch_bounds__(128) k_cloth_membrane(const double* __restrict__ x, const int32_t* __restrict__ tris,
+__global__ void __launch_bounds__(kMemThreads) k_cloth_membrane(const double* __restrict__ x, const int32_t* __restrict__ tris,
                                                         const double* __restrict__ w, const double* __restrict__ at,
                                                         int64_t T, double E, double lam, int32_t* __restrict__ rows,
                                                         int32_t* __restrict__ cols, double* __restrict__ out) {
+  // per warp: each lane's triangle in compressed form (the three 3x3 parts of
+  // the F-Hessian, w, a_t) and its vertices; the warp then writes its
+  // triangles' blocks as one contiguous run, consecutive lanes on consecutive
+  // doubles (a thread writing its own 432-byte run left the stores uncoalesced)
+  __shared__ double sd[kMemThreads / 32][32][kMemStage];
+  __shared__ int32_t sv[kMemThreads / 32][32][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
-  const int32_t v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+  const int64_t t0 = t - lane;  // the warp's first triangle
+  if (t0 >= T) return;          // whole warps only: the lanes below meet at __syncwarp
+  const bool valid = t < T;
+  const int64_t tc = valid ? t : t0;  // an idle lane computes its warp's first triangle again, unused
+  const int32_t v[3] = {tris[3 * tc], tris[3 * tc + 1], tris[3 * tc + 2]};
   double wt[3][2];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) wt[a][0] = w[6 * t + 2 * a], wt[a][1] = w[6 * t + 2 * a + 1];
+  for (int a = 0; a < 3; ++a) wt[a][0] = w[6 * tc + 2 * a], wt[a][1] = w[6 * tc + 2 * a + 1];
   // F = sum_a x_a w_a^T from the edges (w_0 = -(w_1 + w_2)): no cancellation
   // of absolute coordinates against the 1/h-sized weights
   double F[3][2];  // F[x][j]
@@ -158,7 +171,7 @@ __global__ void __launch_bounds__(128) k_cloth_membrane(const double* __restrict
     F[c][0] = e1 * wt[1][0] + e2 * wt[2][0];
     F[c][1] = e1 * wt[1][1] + e2 * wt[2][1];
   }
-  const double s_at = at[t];
+  const double s_at = at[tc];
   double Hd[2][9];  // direction blocks H_00, H_11
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
@@ -188,31 +201,55 @@ __global__ void __launch_bounds__(128) k_cloth_membrane(const double* __restrict
       Hd[1][3 * p + q] += mu2 * F[p][0] * F[q][0];
       H01[3 * p + q] = mu2 * F[p][1] * F[q][0];
     }
-  int64_t k = 6 * t;
+  double* my = sd[warp][lane];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int e = 0; e < 9; ++e) my[e] = Hd[0][e], my[9 + e] = Hd[1][e], my[18 + e] = H01[e];
 #pragma unroll
-    for (int b = a; b < 3; ++b) {
-      const double c00 = wt[a][0] * wt[b][0], c11 = wt[a][1] * wt[b][1];
-      const double c01 = wt[a][0] * wt[b][1], c10 = wt[a][1] * wt[b][0];
-      double B[9];
+  for (int a = 0; a < 3; ++a) my[27 + 2 * a] = wt[a][0], my[28 + 2 * a] = wt[a][1];
+  my[33] = s_at;
 #pragma unroll
-      for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          B[3 * p + q] = s_at * (c00 * Hd[0][3 * p + q] + c11 * Hd[1][3 * p + q] + c01 * H01[3 * p + q] +
-                                 c10 * H01[3 * q + p]);
-      emit(k++, v[a], v[b], B, rows, cols, out);
+  for (int a = 0; a < 3; ++a) sv[warp][lane][a] = v[a];
+  __syncwarp();
+  const int nv = (int)(T - t0 < 32 ? T - t0 : 32);
+  // block k of a triangle is the vertex pair (kPairA[k], kPairB[k])
+  for (int i = lane; i < 54 * nv; i += 32) {
+    const int tri = i / 54, rem = i - 54 * tri, k = rem / 9, e = rem - 9 * k;
+    const int a = k < 3 ? 0 : (k < 5 ? 1 : 2), b = k < 3 ? k : (k < 5 ? k - 2 : 2);
+    const double* d = sd[warp][tri];
+    int p = e / 3, q = e - 3 * (e / 3);
+    if (sv[warp][tri][a] > sv[warp][tri][b]) {  // stored at (min, max): the transpose
+      const int tmp = p;
+      p = q;
+      q = tmp;
     }
+    const double c00 = d[27 + 2 * a] * d[27 + 2 * b], c11 = d[28 + 2 * a] * d[28 + 2 * b];
+    const double c01 = d[27 + 2 * a] * d[28 + 2 * b], c10 = d[28 + 2 * a] * d[27 + 2 * b];
+    out[54 * t0 + i] = d[33] * (c00 * d[3 * p + q] + c11 * d[9 + 3 * p + q] + c01 * d[18 + 3 * p + q] +
+                                c10 * d[18 + 3 * q + p]);
+  }
+  for (int j = lane; j < 6 * nv; j += 32) {
+    const int tri = j / 6, k = j - 6 * tri;
+    const int a = k < 3 ? 0 : (k < 5 ? 1 : 2), b = k < 3 ? k : (k < 5 ? k - 2 : 2);
+    const int32_t va = sv[warp][tri][a], vb = sv[warp][tri][b];
+    if (rows) rows[6 * t0 + j] = min(va, vb);
+    if (cols) cols[6 * t0 + j] = max(va, vb);
+  }
 }
 
 // Bending blocks: one thread per hinge, 10 blocks at base + 10 h.
-__global__ void __launch_bounds__(128) k_cloth_bending(const double* __restrict__ x, const int32_t* __restrict__ hg,
+__global__ void __launch_bounds__(kBendThreads) k_cloth_bending(const double* __restrict__ x, const int32_t* __restrict__ hg,
                                                        const double* __restrict__ kb, int64_t H, int64_t base,
                                                        int32_t* __restrict__ rows, int32_t* __restrict__ cols,
                                                        double* __restrict__ out) {
-  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= H) return;
+  // per warp: each lane's hinge gradient, 2 k_b and vertices, then the warp
+  // writes its hinges' blocks as one contiguous run (see the membrane kernel)
+  __shared__ double sg[kBendThreads / 32][32][13];
+  __shared__ int32_t sv[kBendThreads / 32][32][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t hh = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t h0 = hh - lane;
+  if (h0 >= H) return;  // whole warps only
+  const int64_t h = hh < H ? hh : h0;
   int32_t v[4];
   double P[4][3];
 #pragma unroll
@@ -244,19 +281,39 @@ __global__ void __launch_bounds__(128) k_cloth_bending(const double* __restrict_
     g[2][c] = -le * r1 * n1[c];
     g[3][c] = -le * r2 * n2[c];
   }
-  const double k2 = 2.0 * kb[h];
-  int64_t k = base + 10 * h;
+  double* my = sg[warp][lane];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = a; b < 4; ++b) {
-      double B[9];
+    for (int c = 0; c < 3; ++c) my[3 * a + c] = g[a][c];
+  my[12] = 2.0 * kb[h];
 #pragma unroll
-      for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) B[3 * p + q] = k2 * g[a][p] * g[b][q];
-      emit(k++, v[a], v[b], B, rows, cols, out);
+  for (int a = 0; a < 4; ++a) sv[warp][lane][a] = v[a];
+  __syncwarp();
+  const int nv = (int)(H - h0 < 32 ? H - h0 : 32);
+  // block k of a hinge is the vertex pair (a, b), a <= b, in the order
+  // (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3)
+  for (int i = lane; i < 90 * nv; i += 32) {
+    const int hi = i / 90, rem = i - 90 * hi, k = rem / 9, e = rem - 9 * k;
+    const int a = k < 4 ? 0 : (k < 7 ? 1 : (k < 9 ? 2 : 3));
+    const int b = k < 4 ? k : (k < 7 ? k - 3 : (k < 9 ? k - 5 : 3));
+    const double* d = sg[warp][hi];
+    int p = e / 3, q = e - 3 * (e / 3);
+    if (sv[warp][hi][a] > sv[warp][hi][b]) {  // stored at (min, max): the transpose
+      const int tmp = p;
+      p = q;
+      q = tmp;
     }
+    out[9 * base + 90 * h0 + i] = d[12] * d[3 * a + p] * d[3 * b + q];
+  }
+  for (int j = lane; j < 10 * nv; j += 32) {
+    const int hi = j / 10, k = j - 10 * hi;
+    const int a = k < 4 ? 0 : (k < 7 ? 1 : (k < 9 ? 2 : 3));
+    const int b = k < 4 ? k : (k < 7 ? k - 3 : (k < 9 ? k - 5 : 3));
+    const int32_t va = sv[warp][hi][a], vb = sv[warp][hi][b];
+    if (rows) rows[base + 10 * h0 + j] = min(va, vb);
+    if (cols) cols[base + 10 * h0 + j] = max(va, vb);
+  }
 }
 
 // Mass blocks at base + v.
@@ -375,12 +432,12 @@ int gs_cloth_triplets(gs_ctx ctx, gs_cloth c, const double* x, int32_t* rows, in
   cudaStream_t st = ctx->stream;
   if (c->T) {
     GS_PROF(ctx, GS_K_ELEMENT);
-    cloth::k_cloth_membrane<<<ceil_div(c->T, 128), 128, 0, st>>>(x, c->tris, c->w, c->at, c->T, c->E, c->lam, rows, cols,
+    cloth::k_cloth_membrane<<<ceil_div(c->T, cloth::kMemThreads), cloth::kMemThreads, 0, st>>>(x, c->tris, c->w, c->at, c->T, c->E, c->lam, rows, cols,
                                                                 blocks);
   }
   if (c->H) {
     GS_PROF(ctx, GS_K_ELEMENT);
-    cloth::k_cloth_bending<<<ceil_div(c->H, 128), 128, 0, st>>>(x, c->hinges, c->kb, c->H, 6 * c->T, rows, cols, blocks);
+    cloth::k_cloth_bending<<<ceil_div(c->H, cloth::kBendThreads), cloth::kBendThreads, 0, st>>>(x, c->hinges, c->kb, c->H, 6 * c->T, rows, cols, blocks);
   }
   {
     GS_PROF(ctx, GS_K_ELEMENT);
