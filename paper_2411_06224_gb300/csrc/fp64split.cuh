@@ -33,30 +33,6 @@ __device__ __forceinline__ long long scaled_rint(double v, int b) {
   return bits < 0 ? -q : q;
 }
 
-// T 2^e as the nearest double (ties to even), for |T| < 2^126, in integer
-// arithmetic only: the magnitude is normalised, rounded to 53 bits and packed
-// with its exponent.  Results below the normal range flush to zero.
-__device__ __forceinline__ double int128_scaled_to_double(__int128 T, int e) {
-  if (T == 0) return 0.0;
-  const unsigned long long sign = T < 0 ? 0x8000000000000000ULL : 0ULL;
-  unsigned __int128 M = (unsigned __int128)(T < 0 ? -T : T);
-  const unsigned long long top = (unsigned long long)(M >> 64);
-  const int lz = top ? __clzll(top) : 64 + __clzll((unsigned long long)M);
-  M <<= lz;  // leading one at bit 127
-  unsigned long long mant = (unsigned long long)(M >> 75);  // 53 bits
-  const unsigned __int128 rest = M & ((((unsigned __int128)1) << 75) - 1);
-  const unsigned __int128 half = ((unsigned __int128)1) << 74;
-  int E = 127 - lz + e;  // value = 1.f 2^E
-  if (rest > half || (rest == half && (mant & 1))) {
-    if (++mant == (1ULL << 53)) {
-      mant >>= 1;
-      ++E;
-    }
-  }
-  if (E < -1022) return 0.0;
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
-}
-
 // The digits of y (|y| < 2^55) as BF16 bit patterns, written 128 bytes apart
 // from col (digit 0, the most significant, first), for the tensor-core
 // operand of r.  Balanced digits of y are the plain digits of y + C minus the
@@ -100,7 +76,7 @@ __device__ __forceinline__ void digits128_fast(long long y, int (&d)[8]) {
 // 24 <= S <= 40, in 64-bit integer arithmetic: the 128-bit sum as two words,
 // its magnitude normalised to a leading one in bit 63 of `top`, the bits
 // below it OR-ed into a sticky word.  Results below the normal range flush
-// to zero.  The same value as int128_scaled_to_double on the 128-bit sum.
+// to zero.
 __host__ __device__ __forceinline__ int clz64(unsigned long long x) {
 #ifdef __CUDA_ARCH__
   return __clzll((long long)x);
