@@ -415,7 +415,7 @@ def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live,
                 "flops_per_launch": flops, "bytes_per_launch": nbytes, "avg_launch_ms": tsec * 1e3}
 
     tune_tc = B.gs_tune_get(ctx, B.GS_TUNE_F64_TC)
-    f64tc = (prec == B.GS_PREC_FP64 and nrhs <= 8 and ld % 16 == 0 and tune_tc in (1, 3))
+    f64tc = (prec == B.GS_PREC_FP64 and nrhs <= 8 and ld % 16 == 0 and tune_tc in (1, 3, 4))
     if f64tc:
         if tune_tc == 3:
             # the block lower triangle of every level-0 inverse as 8 base-128
@@ -432,7 +432,7 @@ def kernel_lines(B, ctx, dev, clk, spmv, prec, nrhs, N, V, nnzb, ndom, mp, live,
             dig_bytes = 7 * 2 * n_dom0 * ld * ld
             kname = "k_level0_f64tc"
             kdesc = ("k_level0_f64tc (level-0 MAS apply in FP64 accuracy by exact BF16 digit "
-                     "splitting on tcgen05, + prolongation)")
+                     f"splitting on tcgen05, + prolongation; {256 if tune_tc == 4 else 128} threads per domain)")
         tc_bytes = dig_bytes + 2 * 8 * 3 * V * nrhs
         traffic = recorded_traffic(kname, traffic_key) if traffic_key else None
         apply_line = {"bound": "hbm", "achieved": tc_bytes / t_apply / 1e9, "peak": hbm, "unit": "GB/s",

@@ -333,9 +333,11 @@ int gs_adjoint(gs_ctx ctx, gs_mat mat, gs_mas mas, const double* x, const double
 #define GS_TUNE_BF16_TC 4         /* BF16 level-0 apply on the tensor cores (1, default) or on FP32 cores (0);
                                      the tensor-core form needs 3N a multiple of 16 (N = 16, 32) and nrhs <= 8 */
 #define GS_TUNE_F64_TC 5          /* FP64 MAS apply on the BF16 tensor cores by exact digit splitting (FP64
-                                     accuracy): 1 (default) from 7 BF16 digit matrices per inverse (3.5x
-                                     the bytes of the packed FP64 lower triangle), one CTA per domain; 2 the
-                                     same digits, one persistent warp-specialised CTA per SM for level 0; 3
+                                     accuracy): 4 (default) from 7 BF16 digit matrices per inverse (3.5x
+                                     the bytes of the packed FP64 lower triangle), one CTA of 256 threads
+                                     per domain (two threads per row of the epilogue, four RHS each); 1 the
+                                     same digits, 128 threads per domain; 2 the same digits, one persistent
+                                     warp-specialised CTA per SM for level 0; 3
                                      from each symmetric inverse's block lower triangle, scaled
                                      symmetrically and stored as 8 base-128 digit bytes per entry (1.07x),
                                      expanded to BF16 in shared memory (fewer bytes, more instructions); 0

@@ -125,7 +125,7 @@ def tune(ctx, mat, mas, nrhs=1, reps=10, mixed=False, node_off=None, iters=20, s
     apply = lambda: B.gs_mas_apply(ctx, mas, x, y, nrhs=nrhs)
     if fp64:
         built = B.gs_tune_get(ctx, B.GS_TUNE_F64_TC)  # the value `mas` was built with
-        cands = (3, 0) if built == 3 else (1, 2, 0) if built in (1, 2) else (0,)
+        cands = (3, 0) if built == 3 else (1, 4, 2, 0) if built in (1, 2, 4) else (0,)
         out[NAMES[B.GS_TUNE_F64_TC]] = sweep(ctx, B.GS_TUNE_F64_TC, B.GS_K_MAS_APPLY_L0, apply, reps, cands)
     if not fp64 or B.gs_tune_get(ctx, B.GS_TUNE_F64_TC) == 0:  # the FP64-core kernel's shape
         out[NAMES[B.GS_TUNE_APPLY_RHS]] = sweep(ctx, B.GS_TUNE_APPLY_RHS, B.GS_K_MAS_APPLY_L0, apply, reps)

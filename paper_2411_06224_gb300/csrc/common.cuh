@@ -84,7 +84,7 @@ struct gs_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 1, 1024, 1, 8};  // GS_TUNE_* launch shapes
+  int tune[GS_TUNE_COUNT] = {2, 2, 4, 4096, 1, 4, 1024, 1, 8};  // GS_TUNE_* launch shapes
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // 256 device bytes: [0] error word, [kSpmvCounterWord] SpMV work counter
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB

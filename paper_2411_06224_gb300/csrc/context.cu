@@ -200,7 +200,7 @@ int gs_tune_set(gs_ctx ctx, int32_t param, int32_t value) {
     case GS_TUNE_APPLY_RHS: ok = value == 1 || value == 2 || value == 4 || value == 8; break;
     case GS_TUNE_BATCH_CHUNK: ok = value >= 1024 && value <= 16384 && (value & (value - 1)) == 0; break;
     case GS_TUNE_BF16_TC: ok = value == 0 || value == 1; break;
-    case GS_TUNE_F64_TC: ok = value >= 0 && value <= 3; break;
+    case GS_TUNE_F64_TC: ok = value >= 0 && value <= 4; break;
     case GS_TUNE_SPMV_WS: ok = value == 0 || value == 1; break;
     case GS_TUNE_SPMV_FF_RHS: ok = value == 1 || value == 2 || value == 4 || value == 8; break;
     case GS_TUNE_SPMV_WINDOW: ok = value == 0 || (value >= 256 && value <= 65536 && (value & (value - 1)) == 0); break;

@@ -111,8 +111,8 @@ __global__ void k_split_inverse(const double* __restrict__ inv, int ld, __nv_bfl
 //   z = level-0 product + prolongated coarse results, written per node;
 // kCoarse = true: one coarse-level domain per CTA (job tables), r and z are the
 //   level's contiguous multilevel vectors rl, zl.
-template <bool kCoarse, int kS, int LD>
-__global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* const* __restrict__ dig_tab,
+template <bool kCoarse, int kS, int LD, int kT>
+__global__ void __launch_bounds__(kT) k_level0_f64tc(const __nv_bfloat16* const* __restrict__ dig_tab,
                                                            const int32_t* const* __restrict__ exp_tab,
                                                            const int32_t* __restrict__ job_level,
                                                            const int32_t* __restrict__ job_dom,
@@ -167,11 +167,11 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   }
   // r_d once into registers (entry e = k * ld + j), column exponents by
   // shared-memory atomics, then the digits into the four pair operands
-  constexpr int kPer = 8 * 128 / kThreads;  // entries per thread for ld <= 128
+  constexpr int kPer = 8 * 128 / kT;  // entries per thread for ld <= 128
   double rv[kPer];
 #pragma unroll
   for (int m = 0; m < kPer; ++m) {
-    const int e = tid + m * kThreads;
+    const int e = tid + m * kT;
     const int k = e / ld, j = e - k * ld;
     rv[m] = 0.0;
     if (k < nrhs && k < 8) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   // element (n, kk) of a pair operand at (kk/8)*256 + (n/8)*128 + (n%8)*16 + (kk%8)*2
 #pragma unroll
   for (int m = 0; m < kPer; ++m) {
-    const int e = tid + m * kThreads;
+    const int e = tid + m * kT;
     if (e >= 8 * ld) break;
     const int k = e / ld, j = e - k * ld;
     const long long y = scaled_rint(rv[m], sexp[k] - 1021);  // 0 for zero entries
@@ -200,12 +200,16 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   // Epilogue operands that do not depend on the MMAs, loaded now so that their
   // latency overlaps the tensor-core work: row exponent and the prolongated
   // coarse-level sum per RHS.
-  const int i_row = warp * 32 + lane;
-  const int32_t node_row = (warp * 32 < ld && i_row < ld) ? snode[i_row / 3] : -1;
+  // With 256 threads, warps w and w + 4 share TMEM lane quarter w % 4 and
+  // take the right-hand sides 0..3 and 4..7 of its rows.
+  constexpr int kRpt = 8 * 128 / kT;  // right-hand sides per epilogue thread
+  const int q4 = warp & 3, k0 = (warp >> 2) * kRpt;
+  const int i_row = q4 * 32 + lane;
+  const int32_t node_row = (q4 * 32 < ld && i_row < ld) ? snode[i_row / 3] : -1;
   int a_row = -100000;
-  double coarse_sum[8];
+  double coarse_sum[kRpt];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) coarse_sum[k] = 0.0;
+  for (int k = 0; k < kRpt; ++k) coarse_sum[k] = 0.0;
   if (node_row >= 0) {
     a_row = row_exp[(int64_t)d * ld + i_row];
   }
@@ -216,9 +220,9 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
       if (l >= al.L) break;
       const int64_t item = al.vec_off[l] + al.coarse[l][node_row];
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k < nrhs) {  // the first coarse level assigns: one FP64 add fewer per output
-          const double v = zl[k * lstride + 3 * item + c];
+      for (int k = 0; k < kRpt; ++k)
+        if (k0 + k < nrhs) {  // the first coarse level assigns: one FP64 add fewer per output
+          const double v = zl[(k0 + k) * lstride + 3 * item + c];
           coarse_sum[k] = l == 1 ? v : coarse_sum[k] + v;
         }
     }
@@ -283,35 +287,41 @@ __global__ void __launch_bounds__(kThreads) k_level0_f64tc(const __nv_bfloat16* 
   __syncthreads();
   const bool ok = !*sfail;
   fence_after_sync();
-  if (ok && warp * 32 < ld) {
-    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-    float g[64];  // groups s = 2..9, 8 RHS each: g[8 (s - 2) + k]
-    tmem_ld_32x32b_x16(ta + 0, g);
-    tmem_ld_32x32b_x16(ta + 16, g + 16);
-    tmem_ld_32x32b_x16(ta + 32, g + 32);
-    tmem_ld_32x32b_x16(ta + 48, g + 48);
+  if (ok && q4 * 32 < ld) {
+    const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16);
+    float g[8 * kRpt];  // groups s = 2..9 of this thread's RHS: g[kRpt (s - 2) + k]
+    if constexpr (kRpt == 8) {
+      tmem_ld_32x32b_x16(ta + 0, g);
+      tmem_ld_32x32b_x16(ta + 16, g + 16);
+      tmem_ld_32x32b_x16(ta + 32, g + 32);
+      tmem_ld_32x32b_x16(ta + 48, g + 48);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) tmem_ld_32x32b_x4(ta + 8 * s + k0, g + 4 * s);
+    }
     const int32_t node = node_row;
     if (node >= 0) {
       const int a = a_row;
       const int c = i_row % 3;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k >= nrhs) break;
+      for (int k = 0; k < kRpt; ++k) {
+        const int kk = k0 + k;
+        if (kk >= nrhs) break;
         double v = 0.0;
-        if (sexp[k] && a > -100000) {
+        if (sexp[kk] && a > -100000) {
           // T = hi 2^32 + lo, hi = sum_{s=2..5} G_s 256^(5-s), lo = sum_{s=6..9} G_s 256^(9-s)
           long long hi = 0, lo = 0;
 #pragma unroll
-          for (int s = 0; s < 4; ++s) hi = (hi << 8) + (long long)__float2int_rn(g[8 * s + k]);
+          for (int s = 0; s < 4; ++s) hi = (hi << 8) + (long long)__float2int_rn(g[kRpt * s + k]);
 #pragma unroll
-          for (int s = 4; s < 8; ++s) lo = (lo << 8) + (long long)__float2int_rn(g[8 * s + k]);
-          const int e = a + (sexp[k] - 1021) - 72;  // z = T 2^e, T = hi 2^32 + lo
+          for (int s = 4; s < 8; ++s) lo = (lo << 8) + (long long)__float2int_rn(g[kRpt * s + k]);
+          const int e = a + (sexp[kk] - 1021) - 72;  // z = T 2^e, T = hi 2^32 + lo
           if (e < 900) v = scaled_to_double(hi, lo, e);
         }
         if (kCoarse)
-          z[k * lstride + cbase + i_row] = v;
+          z[kk * lstride + cbase + i_row] = v;
         else
-          z[k * stride + 3 * (int64_t)node + c] = v + coarse_sum[k];
+          z[kk * stride + 3 * (int64_t)node + c] = v + coarse_sum[k];
       }
     }
   }
@@ -610,21 +620,21 @@ __global__ void __launch_bounds__(kPThreads, 1) k_level0_f64tc_persistent(
 
 }  // namespace f64tc
 
-// GS_TUNE_F64_TC: 1 / 2 stream the BF16 digit matrices of this file, 3 the
+// GS_TUNE_F64_TC: 1 / 2 / 4 stream the BF16 digit matrices of this file, 3 the
 // symmetric digit bytes of mas_apply_f64sym.cu; the storage is made when the
 // preconditioner is built for the value set then.
 bool level0_f64tc_usable(gs_ctx ctx, gs_mas mas, int nrhs) {
   if (mas->precision != GS_PREC_FP64 || nrhs < 1 || nrhs > 8) return false;
   const int t = ctx->tune[GS_TUNE_F64_TC];
   if (t == 3) return !mas->dig8.empty();
-  return (t == 1 || t == 2) && !mas->dig64.empty();
+  return (t == 1 || t == 2 || t == 4) && !mas->dig64.empty();
 }
 
 int level0_f64tc_prepare(gs_ctx ctx, gs_mas mas) {
   const int ld = 3 * mas->N;
   const int t = ctx->tune[GS_TUNE_F64_TC];
   if (mas->precision != GS_PREC_FP64 || t == 0) return GS_OK;
-  if (t == 3) return f64sym_shape_ok(mas->N) ? f64sym_prepare(ctx, mas) : GS_OK;
+  if (t == 3) return f64sym_shape_ok(mas->N) ? f64sym_prepare(ctx, mas) : GS_OK;  // 1, 2, 4: BF16 digits
   if (ld % 16 != 0 || ld > f64tc::kM || !mas->dig64.empty()) return GS_OK;
   for (int l = 0; l < mas->L; ++l) {  // every level: level 0 and the coarse levels
     const int64_t n_dom = mas->n_domains[l];
@@ -675,16 +685,25 @@ int level0_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* r, int64
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
   const size_t smem = f64tc::smem_bytes<f64tc::kSlots>(3 * mas->N);
   // 3 N = 96 or 48 (the digit storage is made only for N = 32 and 16)
-#define GS_F64TC_L0(LD)                                                                                     \
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false, f64tc::kSlots, LD>,                             \
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                    \
-  f64tc::k_level0_f64tc<false, f64tc::kSlots, LD><<<mas->n_domains[0], f64tc::kThreads, smem, ctx->stream>>>( \
+#define GS_F64TC_L0(LD, T)                                                                                     \
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<false, f64tc::kSlots, LD, T>,                             \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                       \
+  f64tc::k_level0_f64tc<false, f64tc::kSlots, LD, T><<<mas->n_domains[0], T, smem, ctx->stream>>>(              \
       tabs, etabs, nullptr, nullptr, mas->remap0, mas->N, nrhs, f64tc_levels(mas), r, stride, zl, lstride, z,   \
       ctx->d_flags, skip)
+  const bool wide = ctx->tune[GS_TUNE_F64_TC] == 4;  // 256 threads per domain
   if (mas->N == 32) {
-    GS_F64TC_L0(96);
+    if (wide) {
+      GS_F64TC_L0(96, 256);
+    } else {
+      GS_F64TC_L0(96, 128);
+    }
   } else {
-    GS_F64TC_L0(48);
+    if (wide) {
+      GS_F64TC_L0(48, 256);
+    } else {
+      GS_F64TC_L0(48, 128);
+    }
   }
 #undef GS_F64TC_L0
   GS_CUDA(cudaGetLastError());
@@ -702,9 +721,10 @@ int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, doub
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
 #define GS_F64TC_CO(LD)                                                                                          \
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD>,                             \
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, f64tc::kThreads>,            \
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                         \
-  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD><<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>( \
+  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, f64tc::kThreads>                                          \
+      <<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(                                              \
       tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,             \
       f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags, skip)
   if (mas->N == 32) {

@@ -106,6 +106,17 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 4 consecutive 32-bit columns (as the x16 form).
+__device__ __forceinline__ void tmem_ld_32x32b_x4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Zeros into 32 lanes x 16 consecutive 32-bit columns (the warp's lane
 // quarter, lane field of taddr), waited for before returning.
 __device__ __forceinline__ void tmem_zero_32x32b_x16(uint32_t taddr) {

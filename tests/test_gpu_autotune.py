@@ -52,7 +52,7 @@ def build(B, ctx, s, N=16, L=3, node_off=None):
 def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     for param, bad in ((B.GS_TUNE_SPMV_LANES, 3), (B.GS_TUNE_SPMV_LANES, 0), (B.GS_TUNE_APPLY_RHS, 16), (B.GS_TUNE_SPMV32_LANES, 8),
                        (B.GS_TUNE_BATCH_CHUNK, 3000), (B.GS_TUNE_BATCH_CHUNK, 512), (B.GS_TUNE_BF16_TC, 2),
-                       (B.GS_TUNE_F64_TC, 4), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
+                       (B.GS_TUNE_F64_TC, 5), (B.GS_TUNE_SPMV_WINDOW, 128), (B.GS_TUNE_SPMV_WINDOW, 3000),
                        (B.GS_TUNE_SPMV_WINDOW, 131072), (B.GS_TUNE_SPMV_WS, 2), (B.GS_TUNE_SPMV_FF_RHS, 3),
                        (B.GS_TUNE_COUNT, 2)):
         with pytest.raises(B.GsError):
@@ -60,7 +60,7 @@ def test_tune_set_rejects_values_outside_the_lists(B, ctx):
     from paper_2411_06224_gb300 import autotune
 
     assert autotune.current(ctx) == {"spmv_lanes": 2, "apply_rhs_per_thread": 4, "spmv32_lanes": 2,
-                                     "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 1,
+                                     "batch_chunk": 4096, "bf16_tensor_cores": 1, "fp64_on_tensor_cores": 4,
                                      "spmv_row_window": 1024, "spmv_work_stealing": 1, "spmv_ff_rhs_per_pass": 8}
 
 

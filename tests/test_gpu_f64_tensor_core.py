@@ -121,10 +121,10 @@ def test_digit_split_apply_matches_fp64(B, ctx, n, N, L, nrhs):
     z = torch.empty((nrhs, 3 * V), dtype=torch.float64, device="cuda")
     out, invs = {}, {}
     # symmetric digit bytes; BF16 digit matrices (one CTA per domain, then the
-    # persistent schedule on the same storage); FP64 cores.  Each build's own
+    # persistent schedule and 256-thread CTAs on the same storage); FP64 cores.  Each build's own
     # inverses are exported: builds may differ in the last bits of the coarse
     # level matrices (their sums are not ordered), amplified by the condition.
-    for built, tcs in ((3, (3,)), (1, (1, 2)), (0, (0,))):
+    for built, tcs in ((3, (3,)), (1, (1, 2, 4)), (0, (0,))):
         mat, M, mp = _build(B, ctx, s, N, L, built)
         L_, items = B.gs_mas_info(M)
         inv = [B.gs_mas_export_inverse(ctx, M, l, -(-items[l] // N), N).cpu().numpy() for l in range(L_)]
@@ -135,10 +135,10 @@ def test_digit_split_apply_matches_fp64(B, ctx, n, N, L, nrhs):
             invs[tc] = inv
         B.gs_mas_destroy(M)
         B.gs_mat_destroy(mat)
-    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 1)  # the default
+    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 4)  # the default
     om = mas.build_mas(mp, N, L, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
     ref = {}
-    for tc in (3, 1, 2, 0):
+    for tc in (3, 1, 2, 4, 0):
         # the library's own FP64 inverses (they match the oracle's to ~cond * 1e-16,
         # checked by the parity tests) through the oracle's Eq. 6 apply
         z0 = mas.apply(om.levels, invs[tc], r, om.C)
@@ -146,10 +146,12 @@ def test_digit_split_apply_matches_fp64(B, ctx, n, N, L, nrhs):
         ref[tc] = (z0, absz)
     z0, absz = ref[0]
     assert np.all(np.abs(out[0] - z0) <= 3e-14 * absz + 1e-300)  # FP64 cores: reordered FP64 sums (<= 99 terms)
-    # the two BF16-digit schedules compute the same integers and round them the
-    # same way; they differ only through the order of the FP64 coarse sums
+    # the BF16-digit schedules compute the same integers and round them the same
+    # way; they differ only through the order of the FP64 coarse sums (the two
+    # per-domain forms, 128 or 256 threads, not at all)
     assert np.all(np.abs(out[1] - out[2]) <= 1e-14 * ref[1][1] + 1e-300)
-    for tc, sym in ((1, False), (2, False), (3, True)):
+    assert np.array_equal(out[1], out[4])
+    for tc, sym in ((1, False), (2, False), (4, False), (3, True)):
         z0, absz = ref[tc]
         om.invs = invs[tc]
         bound = split_bound(om, r.reshape(nrhs, V, 3), sym=sym) + 3e-14 * absz
@@ -164,7 +166,7 @@ def test_fp64_pcg_with_digit_split_apply_follows_the_oracle(B, ctx):
     A = pcg.SymmetricMatrix(V, rid, cid, au)
     b = rhs(3 * V, nrhs)
     its = {}
-    for tc in (3, 1, 2, 0):
+    for tc in (3, 1, 2, 4, 0):
         mat, M, mp = _build(B, ctx, s, N, L, tc)
         if tc == 3:
             om = mas.build_mas(mp, N, L, s.adj_ptr, s.adj, s.contacts, rid, cid, au)
@@ -179,6 +181,6 @@ def test_fp64_pcg_with_digit_split_apply_follows_the_oracle(B, ctx):
         its[tc] = list(it)
         B.gs_mas_destroy(M)
         B.gs_mat_destroy(mat)
-    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 1)  # the default
+    B.gs_tune_set(ctx, B.GS_TUNE_F64_TC, 4)  # the default
     print("iterations sym bytes / bf16 digits / persistent / fp64 cores / oracle:", its[3], its[1], its[2], its[0],
           list(it_o))

@@ -60,6 +60,7 @@ def _noalloc(B, ctx, mas, r, z, nrhs):
 _PATHS = [
     (0, 3, 4, 1e-12),   # FP64 accuracy on the tensor cores from symmetric digit bytes, every level
     (0, 1, 4, 1e-12),   # FP64 accuracy on the tensor cores from BF16 digit matrices, every level
+    (0, 4, 8, 1e-12),   # the same with 256-thread CTAs at level 0
     (0, 0, 4, 1e-12),   # FP64 cores
     (0, 1, 12, 1e-12),  # more than 8 RHS: FP64 cores
     (1, 1, 4, 1e-5),    # FP32 inverses
