@@ -720,17 +720,25 @@ int coarse_f64tc_launch(gs_ctx ctx, gs_mas mas, int nrhs, const double* rl, doub
   const size_t smem = f64tc::smem_bytes<f64tc::kSlotsCoarse>(3 * mas->N);
   const auto tabs = (const __nv_bfloat16* const*)mas->d_dig_tab;
   const auto etabs = (const int32_t* const*)(mas->d_dig_tab + 8);
-#define GS_F64TC_CO(LD)                                                                                          \
-  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, f64tc::kThreads>,            \
+#define GS_F64TC_CO(LD, T)                                                                                       \
+  GS_CUDA(cudaFuncSetAttribute(f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, T>,                          \
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                         \
-  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, f64tc::kThreads>                                          \
-      <<<mas->n_coarse_jobs, f64tc::kThreads, smem, ctx->stream>>>(                                              \
+  f64tc::k_level0_f64tc<true, f64tc::kSlotsCoarse, LD, T><<<mas->n_coarse_jobs, T, smem, ctx->stream>>>(         \
       tabs, etabs, mas->d_coarse_jobs, mas->d_coarse_jobs + mas->n_coarse_jobs, nullptr, mas->N, nrhs,             \
       f64tc_levels(mas), rl, 0, nullptr, lstride, zl, ctx->d_flags, skip)
+  const bool wide = ctx->tune[GS_TUNE_F64_TC] == 4;  // 256 threads per domain
   if (mas->N == 32) {
-    GS_F64TC_CO(96);
+    if (wide) {
+      GS_F64TC_CO(96, 256);
+    } else {
+      GS_F64TC_CO(96, 128);
+    }
   } else {
-    GS_F64TC_CO(48);
+    if (wide) {
+      GS_F64TC_CO(48, 256);
+    } else {
+      GS_F64TC_CO(48, 128);
+    }
   }
 #undef GS_F64TC_CO
   GS_CUDA(cudaGetLastError());
