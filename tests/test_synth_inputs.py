@@ -55,3 +55,28 @@ def test_batch_blocks_stay_inside_their_system():
     src = np.repeat(np.arange(b.n_vertices), np.diff(b.adj_ptr))
     assert np.all(sys_of[src] == sys_of[b.adj])
     assert np.all(sys_of[b.contacts[:, 0]] == sys_of[b.contacts[:, 1]])
+
+
+def test_unique_sorted_is_numpys_unique():
+    from synth.mesh import unique_sorted
+
+    rng = np.random.default_rng(8)
+    for n, hi in ((0, 5), (1, 5), (1000, 10), (100_000, 1 << 40)):
+        a = rng.integers(0, hi, n)
+        assert np.array_equal(unique_sorted(a), np.unique(a))
+
+
+def test_coupled_scene_without_fem_blocks_keeps_every_other_input():
+    from synth.abd import make_abd_scene
+
+    a = make_abd_scene(n=8, n_bodies=9, n_contacts=400, seed=31)
+    b = make_abd_scene(n=8, n_bodies=9, n_contacts=400, seed=31, fem_blocks=False)
+    for f in ("X", "adj_ptr", "adj", "contacts", "body_of_node", "xbar"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    # the inputs that remain are the full scene's minus the FEM element and mass blocks
+    fem = (a.rows < a.n_fem) & (a.cols < a.n_fem)
+    key = lambda r, c, blk: sorted(zip(r.tolist(), c.tolist(), np.round(blk.reshape(len(r), -1), 6).tolist()))
+    contacts_fem = (b.rows < b.n_fem) & (b.cols < b.n_fem)  # FEM-FEM contact pairs only
+    assert key(a.rows[~fem], a.cols[~fem], a.blocks[~fem]) == key(b.rows[~contacts_fem], b.cols[~contacts_fem],
+                                                                  b.blocks[~contacts_fem])
+    assert b.fem_x.shape == (a.n_fem, 3) and b.fem_tets.shape[1] == 4
