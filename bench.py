@@ -93,6 +93,8 @@ def parse():
                    help="instead of the solve benchmark: build the Newton form's elastic cube at GRID^3, assemble "
                         "its Hessian once and refill it --refills times (a short run for ncu captures)")
     p.add_argument("--refills", type=int, default=3)
+    p.add_argument("--cloth-probe", type=int, default=0, metavar="N",
+                   help="only the cloth element-Hessian kernels on an N x N sheet, --refills times (for captures)")
     p.add_argument("--micro", action="store_true",
                    help="instead of the solve benchmark: the paper's reduction and SpMV microbenchmarks")
     p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)  # worker mode
@@ -707,6 +709,15 @@ def abd_form(args, B, dev, clk):
 # and 10 blocks of 9 products of 2
 CLOTH_FLOP_TRI = 36 + 2 * 36 + 27 * 3 + 6 * (4 + 9 * 8)
 CLOTH_FLOP_HINGE = 65 + 12 * 3 + 10 * 9 * 2
+# FP64 instructions (DFMA + DMUL + DADD, per thread) per element as the
+# hardware counters show them for k_cloth_membrane and k_cloth_bending on the
+# 512^2 sheet: the kernels issue more than the source count above (the
+# blocks are written lane-per-entry, so their weight products repeat, and
+# square roots and divisions expand into several FP64 instructions).  The FP64
+# pipe is the bound: it issues FP64_FMA_PER_CLK_PER_SM thread instructions
+# per clock per SM whatever the instruction.
+CLOTH_FP64_INST_TRI = 641.5
+CLOTH_FP64_INST_HINGE = 277.0
 
 
 def cloth_element_line(args, B, dev, stream, clk):
@@ -754,15 +765,18 @@ def cloth_element_line(args, B, dev, stream, clk):
     T, H, V = len(tris), len(hg), X.shape[0]
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    fp64_peak = props.multi_processor_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    inst_peak = props.multi_processor_count * FP64_FMA_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9  # G instr/s
+    inst = CLOTH_FP64_INST_TRI * T + CLOTH_FP64_INST_HINGE * H
     flops = CLOTH_FLOP_TRI * T + CLOTH_FLOP_HINGE * H
     nbytes = T * (3 * 24 + 48 + 8 + 12 + 6 * 80) + H * (4 * 24 + 16 + 8 + 10 * 80) + V * (8 + 80)
     out = {"workload": f"cloth {n}x{n}: {T} triangles, {H} hinges, {V} vertices -> {nt} triplets",
            "value": (T + H) / sec, "unit": "elements/s (triangles + hinges)", "ms_per_launch_sequence": sec * 1e3,
-           "roofline": {"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": flops / sec / 1e12 / fp64_peak, "traffic": None, "flops_per_launch": flops,
-                        "bytes_per_launch": nbytes, "hbm_gbs": nbytes / sec / 1e9,
-                        "kernel": "k_cloth_membrane + k_cloth_bending + k_cloth_mass_blocks (FP64)"}}
+           "roofline": {"bound": "alu", "achieved": inst / sec / 1e9, "peak": inst_peak,
+                        "unit": "G FP64 instr/s", "frac": inst / sec / 1e9 / inst_peak, "traffic": None,
+                        "fp64_instr_per_launch": inst, "source_flops_per_launch": flops,
+                        "source_tflops": flops / sec / 1e12, "bytes_per_launch": nbytes,
+                        "hbm_gbs": nbytes / sec / 1e9,
+                        "kernel": "k_cloth_membrane + k_cloth_bending + k_cloth_mass_blocks (FP64 pipe)"}}
     if not args.no_cpu_baseline:
         from oracle import cloth as ocloth
 
@@ -813,6 +827,40 @@ def element_probe(args):
                       "refills": args.refills}))
     B.gs_mat_destroy(m)
     B.gs_fem_destroy(f)
+    B.gs_destroy(ctx)
+
+
+def cloth_probe(args):
+    """The stiff-cloth sheet of the precision form at --cloth-probe vertices per
+    edge: rest data once, then the element Hessians --refills times; prints
+    the counts."""
+    import numpy as np
+    import torch
+
+    from paper_2411_06224_gb300.build import build
+    from synth.cloth import hinges, sheet
+
+    build()
+    from paper_2411_06224_gb300 import binding as B
+
+    n = args.cloth_probe
+    X, tris = sheet(n)
+    hg = hinges(tris)
+    rng = np.random.default_rng(1003)
+    h = 1.0 / (n - 1)
+    sh = rng.uniform(0.0, 0.1)
+    x = X @ np.array([[1.02, sh, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]).T + rng.normal(0.0, 0.01 * h, X.shape)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    ctx = B.gs_create(0)
+    c = B.gs_cloth_create(ctx, t(X, torch.float64), t(tris, torch.int32), t(hg, torch.int32), 1e8, 0.05e6, 1e-3,
+                          200.0, 0.01)
+    xd = t(x, torch.float64)
+    for _ in range(args.refills):
+        B.gs_cloth_triplets(ctx, c, xd)
+    torch.cuda.synchronize()
+    print(json.dumps({"triangles": int(len(tris)), "hinges": int(len(hg)), "triplets": B.gs_cloth_info(c),
+                      "launch_sequences": args.refills}))
+    B.gs_cloth_destroy(c)
     B.gs_destroy(ctx)
 
 
@@ -980,6 +1028,8 @@ def main():
         return micro(args)
     if args.element_probe:
         return element_probe(args)
+    if args.cloth_probe:
+        return cloth_probe(args)
 
     import numpy as np
     import torch
