@@ -701,23 +701,23 @@ def abd_form(args, B, dev, clk):
 
 
 # FP64 operations per element of the cloth kernels, counted from their source
-# (FMA = 2; square roots and divisions as 1): triangle = F (18 FMA), two
-# directions (norm, coefficients, 9 entries of c_f f f^T + c_i I: 36 each),
-# the shear terms (27 entries, 3 each) and 6 blocks (4 weight products, 9
-# entries of 4 weighted terms and the area scale: 8 each); hinge = edge
-# vectors, normals, norms and projections (65), gradients (12 entries, 3 each)
-# and 10 blocks of 9 products of 2
-CLOTH_FLOP_TRI = 36 + 2 * 36 + 27 * 3 + 6 * (4 + 9 * 8)
-CLOTH_FLOP_HINGE = 65 + 12 * 3 + 10 * 9 * 2
+# (FMA = 2; square roots and divisions as 1): triangle = F (24), two
+# directions (norm, coefficients, strain limit, 6 entries of the symmetric
+# block: 57 each), the shear scale and cross block (14), H_01 + H_01^T (6),
+# 3 symmetric vertex blocks (3 weight products, 6 entries of 5: 33 each) and
+# 3 others (4 weight products, 9 entries of 7: 67 each); hinge = edge vectors,
+# normals, norms, projections and gradients (94), 2 k_b g (13) and 10 blocks
+# of 9 products
+CLOTH_FLOP_TRI = 24 + 2 * 57 + 14 + 6 + 3 * 33 + 3 * 67
+CLOTH_FLOP_HINGE = 94 + 13 + 10 * 9
 # FP64 instructions (DFMA + DMUL + DADD, per thread) per element as the
 # hardware counters show them for k_cloth_membrane and k_cloth_bending on the
-# 512^2 sheet: the kernels issue more than the source count above (the
-# blocks are written lane-per-entry, so their weight products repeat, and
-# square roots and divisions expand into several FP64 instructions).  The FP64
-# pipe is the bound: it issues FP64_FMA_PER_CLK_PER_SM thread instructions
-# per clock per SM whatever the instruction.
-CLOTH_FP64_INST_TRI = 641.5
-CLOTH_FP64_INST_HINGE = 277.0
+# 512^2 sheet (square roots and divisions expand into several FP64
+# instructions; the source count above takes them as one).  The FP64 pipe is
+# the bound: it issues FP64_FMA_PER_CLK_PER_SM thread instructions per clock
+# per SM whatever the instruction.
+CLOTH_FP64_INST_TRI = 300.0
+CLOTH_FP64_INST_HINGE = 181.0
 
 
 def cloth_element_line(args, B, dev, stream, clk):
@@ -851,15 +851,26 @@ def cloth_probe(args):
     sh = rng.uniform(0.0, 0.1)
     x = X @ np.array([[1.02, sh, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]).T + rng.normal(0.0, 0.01 * h, X.shape)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
-    ctx = B.gs_create(0)
+    stream = torch.cuda.Stream()
+    ctx = B.gs_create(0, stream)
     c = B.gs_cloth_create(ctx, t(X, torch.float64), t(tris, torch.int32), t(hg, torch.int32), 1e8, 0.05e6, 1e-3,
                           200.0, 0.01)
     xd = t(x, torch.float64)
-    for _ in range(args.refills):
-        B.gs_cloth_triplets(ctx, c, xd)
+    B.gs_cloth_triplets(ctx, c, xd)
+    nt = B.gs_cloth_info(c)
+    rows = torch.empty(nt, dtype=torch.int32, device="cuda")
+    cols = torch.empty(nt, dtype=torch.int32, device="cuda")
+    blocks = torch.empty((nt, 3, 3), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
-    print(json.dumps({"triangles": int(len(tris)), "hinges": int(len(hg)), "triplets": B.gs_cloth_info(c),
-                      "launch_sequences": args.refills}))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.refills):
+        B.lib().gs_cloth_triplets(ctx, c, ctypes_ptr(xd), ctypes_ptr(rows), ctypes_ptr(cols), ctypes_ptr(blocks))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"triangles": int(len(tris)), "hinges": int(len(hg)), "triplets": nt,
+                      "launch_sequences": args.refills,
+                      "ms_per_launch_sequence": e0.elapsed_time(e1) / max(args.refills, 1)}))
     B.gs_cloth_destroy(c)
     B.gs_destroy(ctx)
 

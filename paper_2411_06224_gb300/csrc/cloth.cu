@@ -43,9 +43,9 @@ namespace gs {
 namespace cloth {
 
 constexpr double kShear = 0.3;  // shear stiffness relative to lam
-constexpr int kMemThreads = 128;  // membrane kernel block
-constexpr int kMemStage = 35;     // doubles staged per triangle (34 used; odd stride)
+constexpr int kMemThreads = 64;  // membrane kernel block: 27 KB of staged blocks
 constexpr int kBendThreads = 128;
+constexpr int kBendStage = 25;  // doubles staged per hinge (24 used; odd stride)
 
 // Rest data per triangle: w and a_t; flags a repeated or out-of-range vertex
 // and a degenerate rest triangle.
@@ -140,16 +140,21 @@ __device__ __forceinline__ void emit(int64_t k, int32_t va, int32_t vb, const do
     for (int y = 0; y < 3; ++y) o[3 * x + y] = sw ? B[3 * y + x] : B[3 * x + y];
 }
 
-// Membrane blocks: one thread per triangle, 6 blocks at 6 t.
+// Membrane blocks: one thread per triangle, 6 blocks at 6 t.  The owner
+// thread forms its 6 blocks and stages them, already in emission layout, for
+// the warp's coalesced write.  The kernel is bound by the FP64 pipe, not by
+// its bytes, so the F-Hessian is kept in its structured form (symmetric
+// direction blocks, the shear cross block) and scaled by a_t through its
+// coefficients.
 __global__ void __launch_bounds__(kMemThreads) k_cloth_membrane(const double* __restrict__ x, const int32_t* __restrict__ tris,
                                                         const double* __restrict__ w, const double* __restrict__ at,
                                                         int64_t T, double E, double lam, int32_t* __restrict__ rows,
                                                         int32_t* __restrict__ cols, double* __restrict__ out) {
-  // per warp: each lane's triangle in compressed form (the three 3x3 parts of
-  // the F-Hessian, w, a_t) and its vertices; the warp then writes its
-  // triangles' blocks as one contiguous run, consecutive lanes on consecutive
-  // doubles (a thread writing its own 432-byte run left the stores uncoalesced)
-  __shared__ double sd[kMemThreads / 32][32][kMemStage];
+  // per warp: the lanes' triangles' blocks back to back (54 doubles each) and
+  // their vertices; the warp then writes them as one contiguous run,
+  // consecutive lanes on consecutive doubles (a thread writing its own
+  // 432-byte run left the stores uncoalesced)
+  __shared__ double st[kMemThreads / 32][32 * 54];
   __shared__ int32_t sv[kMemThreads / 32][32][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,75 +163,95 @@ __global__ void __launch_bounds__(kMemThreads) k_cloth_membrane(const double* __
   const bool valid = t < T;
   const int64_t tc = valid ? t : t0;  // an idle lane computes its warp's first triangle again, unused
   const int32_t v[3] = {tris[3 * tc], tris[3 * tc + 1], tris[3 * tc + 2]};
-  double wt[3][2];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) wt[a][0] = w[6 * tc + 2 * a], wt[a][1] = w[6 * tc + 2 * a + 1];
-  // F = sum_a x_a w_a^T from the edges (w_0 = -(w_1 + w_2)): no cancellation
-  // of absolute coordinates against the 1/h-sized weights
+  const double w10 = w[6 * tc + 2], w11 = w[6 * tc + 3], w20 = w[6 * tc + 4], w21 = w[6 * tc + 5];
+  // F = (x_1 - x_0) w_1^T + (x_2 - x_0) w_2^T (w_0 = -(w_1 + w_2)): no
+  // cancellation of absolute coordinates against the 1/h-sized weights
   double F[3][2];  // F[x][j]
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double x0 = x[3 * (int64_t)v[0] + c];
     const double e1 = x[3 * (int64_t)v[1] + c] - x0, e2 = x[3 * (int64_t)v[2] + c] - x0;
-    F[c][0] = e1 * wt[1][0] + e2 * wt[2][0];
-    F[c][1] = e1 * wt[1][1] + e2 * wt[2][1];
+    F[c][0] = e1 * w10 + e2 * w20;
+    F[c][1] = e1 * w11 + e2 * w21;
   }
   const double s_at = at[tc];
-  double Hd[2][9];  // direction blocks H_00, H_11
+  // the F-Hessian times a_t: symmetric direction blocks H_00, H_11 (upper
+  // triangles, index u(p, q)) and the shear cross block H_01 = mu2 f_1 f_0^T
+  constexpr int kU[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  const double mu2 = 2.0 * kShear * lam * s_at;
+  double Hd[2][6];
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
     const double f[3] = {F[0][d], F[1][d], F[2][d]};
     const double s2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
-    const double s = sqrt(s2);
-    const double across = fmax(1.0 - 1.0 / s, 0.0);
-    double ci = 2.0 * lam * across;                  // coefficient of I
-    double cf = 2.0 * lam * (1.0 - across) / s2;     // coefficient of f f^T
-    if (s > 1.0) {                                  // strain limit, Sec. 4
-      ci += 3.0 * E * (1.0 - 1.0 / s) * (s - 1.0);
-      cf += 3.0 * E * (s2 - 1.0) / (s2 * s);
+    const double is = rsqrt(s2), is2 = is * is, s = s2 * is;
+    const double across = fmax(1.0 - is, 0.0);
+    double ci = 2.0 * lam * across;                // coefficient of I
+    double cf = 2.0 * lam * (1.0 - across) * is2;  // coefficient of f f^T
+    if (s > 1.0) {                                 // strain limit, Sec. 4
+      ci += 3.0 * E * (1.0 - is) * (s - 1.0);
+      cf += 3.0 * E * (s2 - 1.0) * is2 * is;
     }
+    ci *= s_at;
+    cf *= s_at;
+    const double g[3] = {F[0][1 - d], F[1][1 - d], F[2][1 - d]};  // shear: g = [f_1; f_0]
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p) {
+      const double cfp = cf * f[p], mgp = mu2 * g[p];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) Hd[d][3 * p + q] = cf * f[p] * f[q] + (p == q ? ci : 0.0);
+      for (int q = p; q < 3; ++q) Hd[d][kU[p][q]] = fma(cfp, f[q], fma(mgp, g[q], p == q ? ci : 0.0));
+    }
   }
-  // shear Gauss-Newton: g = [f_1; f_0]
-  const double mu2 = 2.0 * kShear * lam;
-  double H01[9];  // H[f_0 rows][f_1 cols] = mu2 f_1 f_0^T
+  double H01[3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const double mgp = mu2 * F[p][1];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) H01[p][q] = mgp * F[q][0];
+  }
+  // block (a, b) = sum_{i,j} w_a[i] w_b[j] H_ij (H_10 = H_01^T), each block
+  // from its own weights: forming some blocks from the others through
+  // w_0 = -(w_1 + w_2) cancels when the two directions' stiffnesses differ
+  // by orders of magnitude (the strain limit against the stretching)
+  double* my = st[warp] + 54 * lane;
+  double hx[6];  // H_01 + H_01^T, upper triangle
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      Hd[0][3 * p + q] += mu2 * F[p][1] * F[q][1];
-      Hd[1][3 * p + q] += mu2 * F[p][0] * F[q][0];
-      H01[3 * p + q] = mu2 * F[p][1] * F[q][0];
-    }
-  double* my = sd[warp][lane];
+    for (int q = p; q < 3; ++q) hx[kU[p][q]] = H01[p][q] + H01[q][p];
+  auto diag = [&](int k, double wa0, double wa1) {  // symmetric (a, a)
+    const double c00 = wa0 * wa0, c11 = wa1 * wa1, c01 = wa0 * wa1;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) my[e] = Hd[0][e], my[9 + e] = Hd[1][e], my[18 + e] = H01[e];
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-  for (int a = 0; a < 3; ++a) my[27 + 2 * a] = wt[a][0], my[28 + 2 * a] = wt[a][1];
-  my[33] = s_at;
+      for (int q = p; q < 3; ++q)
+        my[9 * k + 3 * p + q] = my[9 * k + 3 * q + p] =
+            fma(c00, Hd[0][kU[p][q]], fma(c11, Hd[1][kU[p][q]], c01 * hx[kU[p][q]]));
+  };
+  // (a, b), a < b, stored transposed when v_a > v_b
+  auto off = [&](int k, double wa0, double wa1, double wb0, double wb1, bool sw) {
+    const double c00 = wa0 * wb0, c11 = wa1 * wb1, c01 = wa0 * wb1, c10 = wa1 * wb0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double bpq =
+            fma(c00, Hd[0][kU[p][q]], fma(c11, Hd[1][kU[p][q]], fma(c01, H01[p][q], c10 * H01[q][p])));
+        my[9 * k + (sw ? 3 * q + p : 3 * p + q)] = bpq;
+      }
+  };
+  const double w00 = w[6 * tc], w01 = w[6 * tc + 1];
+  diag(0, w00, w01);
+  off(1, w00, w01, w10, w11, v[0] > v[1]);
+  off(2, w00, w01, w20, w21, v[0] > v[2]);
+  diag(3, w10, w11);
+  off(4, w10, w11, w20, w21, v[1] > v[2]);
+  diag(5, w20, w21);
 #pragma unroll
   for (int a = 0; a < 3; ++a) sv[warp][lane][a] = v[a];
   __syncwarp();
   const int nv = (int)(T - t0 < 32 ? T - t0 : 32);
-  // block k of a triangle is the vertex pair (kPairA[k], kPairB[k])
-  for (int i = lane; i < 54 * nv; i += 32) {
-    const int tri = i / 54, rem = i - 54 * tri, k = rem / 9, e = rem - 9 * k;
-    const int a = k < 3 ? 0 : (k < 5 ? 1 : 2), b = k < 3 ? k : (k < 5 ? k - 2 : 2);
-    const double* d = sd[warp][tri];
-    int p = e / 3, q = e - 3 * (e / 3);
-    if (sv[warp][tri][a] > sv[warp][tri][b]) {  // stored at (min, max): the transpose
-      const int tmp = p;
-      p = q;
-      q = tmp;
-    }
-    const double c00 = d[27 + 2 * a] * d[27 + 2 * b], c11 = d[28 + 2 * a] * d[28 + 2 * b];
-    const double c01 = d[27 + 2 * a] * d[28 + 2 * b], c10 = d[28 + 2 * a] * d[27 + 2 * b];
-    out[54 * t0 + i] = d[33] * (c00 * d[3 * p + q] + c11 * d[9 + 3 * p + q] + c01 * d[18 + 3 * p + q] +
-                                c10 * d[18 + 3 * q + p]);
-  }
+  for (int i = lane; i < 54 * nv; i += 32) out[54 * t0 + i] = st[warp][i];
   for (int j = lane; j < 6 * nv; j += 32) {
     const int tri = j / 6, k = j - 6 * tri;
     const int a = k < 3 ? 0 : (k < 5 ? 1 : 2), b = k < 3 ? k : (k < 5 ? k - 2 : 2);
@@ -241,9 +266,10 @@ __global__ void __launch_bounds__(kBendThreads) k_cloth_bending(const double* __
                                                        const double* __restrict__ kb, int64_t H, int64_t base,
                                                        int32_t* __restrict__ rows, int32_t* __restrict__ cols,
                                                        double* __restrict__ out) {
-  // per warp: each lane's hinge gradient, 2 k_b and vertices, then the warp
-  // writes its hinges' blocks as one contiguous run (see the membrane kernel)
-  __shared__ double sg[kBendThreads / 32][32][13];
+  // per warp: each lane's hinge gradient g and 2 k_b g and its vertices,
+  // then the warp writes its hinges' blocks as one contiguous run (see the
+  // membrane kernel); an entry costs one DMUL
+  __shared__ double sg[kBendThreads / 32][32][kBendStage];
   __shared__ int32_t sv[kBendThreads / 32][32][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t hh = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,13 +290,17 @@ __global__ void __launch_bounds__(kBendThreads) k_cloth_bending(const double* __
   // n_1 = e x u1, n_2 = u2 x e
   const double n1[3] = {e[1] * u1[2] - e[2] * u1[1], e[2] * u1[0] - e[0] * u1[2], e[0] * u1[1] - e[1] * u1[0]};
   const double n2[3] = {u2[1] * e[2] - u2[2] * e[1], u2[2] * e[0] - u2[0] * e[2], u2[0] * e[1] - u2[1] * e[0]};
+  // one reciprocal square root and one division (each expands into several
+  // FP64-pipe instructions): 1/|e| and 1/(|n_1|^2 |n_2|^2)
   const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-  const double le = sqrt(ee);
-  const double r1 = 1.0 / (n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2]);
-  const double r2 = 1.0 / (n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
+  const double ile = rsqrt(ee), le = ee * ile;
+  const double m1 = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+  const double m2 = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
+  const double im = 1.0 / (m1 * m2);
+  const double r1 = m2 * im, r2 = m1 * im;  // 1 / |n_i|^2
   // projections onto e / |e|: (o_i - e_1) . e = u_i . e - |e|^2, (o_i - e_0) . e = u_i . e
-  const double p1 = (u1[0] * e[0] + u1[1] * e[1] + u1[2] * e[2]) / le;
-  const double p2 = (u2[0] * e[0] + u2[1] * e[1] + u2[2] * e[2]) / le;
+  const double p1 = (u1[0] * e[0] + u1[1] * e[1] + u1[2] * e[2]) * ile;
+  const double p2 = (u2[0] * e[0] + u2[1] * e[1] + u2[2] * e[2]) * ile;
   const double a1 = -(p1 - le) * r1, a2 = -(p2 - le) * r2;  // d theta / d e_0 = a1 n1 + a2 n2
   const double b1 = p1 * r1, b2 = p2 * r2;                  // d theta / d e_1 = b1 n1 + b2 n2
   double g[4][3];
@@ -282,11 +312,11 @@ __global__ void __launch_bounds__(kBendThreads) k_cloth_bending(const double* __
     g[3][c] = -le * r2 * n2[c];
   }
   double* my = sg[warp][lane];
+  const double k2 = 2.0 * kb[h];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) my[3 * a + c] = g[a][c];
-  my[12] = 2.0 * kb[h];
+    for (int c = 0; c < 3; ++c) my[3 * a + c] = k2 * g[a][c], my[12 + 3 * a + c] = g[a][c];
 #pragma unroll
   for (int a = 0; a < 4; ++a) sv[warp][lane][a] = v[a];
   __syncwarp();
@@ -304,7 +334,7 @@ __global__ void __launch_bounds__(kBendThreads) k_cloth_bending(const double* __
       p = q;
       q = tmp;
     }
-    out[9 * base + 90 * h0 + i] = d[12] * d[3 * a + p] * d[3 * b + q];
+    out[9 * base + 90 * h0 + i] = d[3 * a + p] * d[12 + 3 * b + q];
   }
   for (int j = lane; j < 10 * nv; j += 32) {
     const int hi = j / 10, k = j - 10 * hi;
