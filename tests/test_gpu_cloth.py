@@ -53,8 +53,8 @@ def block_close(got, ref, rtol=1e-11):
     return np.abs(got - ref) <= rtol * scale + 1e-300
 
 
-def device_triplets(B, ctx, X, x, tris, hg):
-    c = B.gs_cloth_create(ctx, dev(X, torch.float64), dev(tris, torch.int32), dev(hg, torch.int32), **PARAMS)
+def device_triplets(B, ctx, X, x, tris, hg, params=PARAMS):
+    c = B.gs_cloth_create(ctx, dev(X, torch.float64), dev(tris, torch.int32), dev(hg, torch.int32), **params)
     try:
         r, cc, b = B.gs_cloth_triplets(ctx, c, dev(x, torch.float64))
         return r.cpu().numpy(), cc.cpu().numpy(), b.cpu().numpy()
@@ -74,6 +74,24 @@ def test_cloth_triplets_match_the_oracle_one_by_one(B, ctx, n, stretch):
     assert np.array_equal(r, r0) and np.array_equal(c, c0)
     ok = block_close(b, b0)
     assert ok.all(), np.argwhere(~ok)[:5]
+
+
+def test_stiffness_contrast_keeps_every_block_accurate(B, ctx):
+    # E / lam = 2e5 with only the x direction past the strain limit: a vertex
+    # block mixing mostly the soft direction is tiny next to the stiff ones,
+    # and must still carry its own relative accuracy (a block formed as the
+    # difference of two large ones would not)
+    X, x, tris, hg = deformed(17)
+    x = x.copy()
+    x[:, 0] *= 1.3 / 1.02
+    params = dict(PARAMS, E=1e10)
+    r, c, b = device_triplets(B, ctx, X, x, tris, hg, params)
+    r0, c0, b0 = cloth.cloth_triplets(X, x, tris, hg, **params)
+    assert np.array_equal(r, r0) and np.array_equal(c, c0)
+    m = 6 * len(tris)  # the membrane blocks, then bending and masses at the usual bound
+    ok = block_close(b[:m], b0[:m], rtol=1e-12)
+    assert ok.all(), np.argwhere(~ok)[:5]
+    assert block_close(b[m:], b0[m:]).all()
 
 
 def test_full_sheet_sampled_elements_and_masses(B, ctx):
