@@ -244,8 +244,10 @@ int gs_mas_apply(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrh
  * Arguments and result: as gs_mas_apply.  Limit: 2 * nrhs * 3 * (items of
  * all levels >= 1, domains padded to N) doubles must not exceed 524,288;
  * otherwise GS_ERR_INVALID with a message naming the sizes.
- * The first call on each device looks the array's address up (with that
- * device current) and should be made before any stream capture begins.
+ * The first call on each context looks the array's address up (with that
+ * context's device current) and keeps it in the context; make it before any
+ * stream capture begins.  A context created after a device reset looks the
+ * address up again.
  * Calls share the array and clear its restricted part on entry; calls whose
  * work overlaps on the GPU race on it. */
 int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs);

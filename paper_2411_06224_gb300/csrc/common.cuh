@@ -88,6 +88,7 @@ struct gs_ctx_s {
   cudaStream_t capture_stream = nullptr;  // private stream for CUDA-graph capture
   int* d_flags = nullptr;     // 256 device bytes: [0] error word, [kSpmvCounterWord] SpMV work counter
   int* h_pinned = nullptr;    // pinned host staging (small readbacks), 4 KiB
+  double* noalloc_scratch = nullptr;  // gs_mas_apply_noalloc's fixed array in this context
   std::vector<gs::Buffer> scratch;  // named scratch slots, reused across calls
   int64_t n_allocs = 0;       // device allocations made through alloc() so far
   int64_t alloc_bytes = 0;    // and their total size

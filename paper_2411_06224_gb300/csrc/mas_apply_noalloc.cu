@@ -25,7 +25,6 @@
 // gs_mas_apply.
 // With the profiler switched on (gs_profile_begin) the library may create
 // CUDA events; it is off unless the caller turns it on.
-#include <mutex>
 
 #include "common.cuh"
 
@@ -43,25 +42,22 @@ int mas_apply_launch(gs_ctx ctx, gs_mas mas, const double* r, double* z, int nrh
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
-std::mutex g_lock;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device` (current), looked up once.
-int scratch_address(int device, double** out) {
-  std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_addr[device]) {
+// Device address of the scratch array, looked up at the context's first call
+// (with its device current) and kept in the context: a context made after a
+// device reset looks it up again, and later calls make no CUDA call for it
+// (so they may run under stream capture).
+int scratch_address(gs_ctx ctx, double** out) {
+  if (!ctx->noalloc_scratch) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_level_scratch);
     if (e != cudaSuccess) {
-      set_error("gs_mas_apply_noalloc: cudaGetSymbolAddress failed on device %d: %s", device,
+      set_error("gs_mas_apply_noalloc: cudaGetSymbolAddress failed on device %d: %s", ctx->device,
                 cudaGetErrorString(e));
       return GS_ERR_CUDA;
     }
-    g_addr[device] = (double*)p;
+    ctx->noalloc_scratch = (double*)p;
   }
-  *out = g_addr[device];
+  *out = ctx->noalloc_scratch;
   return GS_OK;
 }
 
@@ -71,8 +67,6 @@ int scratch_address(int device, double** out) {
 extern "C" int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, double* z, int32_t nrhs) {
   GS_CHECK(ctx && mas && r && z && r != z, GS_ERR_INVALID, "gs_mas_apply_noalloc: null or aliased argument");
   GS_CHECK(nrhs >= 1, GS_ERR_INVALID, "gs_mas_apply_noalloc: nrhs %d", nrhs);
-  GS_CHECK(ctx->device >= 0 && ctx->device < gs::kMaxDevices, GS_ERR_UNSUPPORTED,
-           "gs_mas_apply_noalloc: device %d", ctx->device);
   const size_t per = (size_t)nrhs * 3 * (size_t)std::max<int64_t>(mas->vec_items, 1);
   GS_CHECK(2 * per <= gs::kNoAllocDoubles, GS_ERR_INVALID,
            "gs_mas_apply_noalloc: needs %zu doubles of coarse-level scratch (2 x %d RHS x 3 x %lld items), "
@@ -80,7 +74,7 @@ extern "C" int gs_mas_apply_noalloc(gs_ctx ctx, gs_mas mas, const double* r, dou
            2 * per, nrhs, (long long)mas->vec_items, gs::kNoAllocDoubles);
   GS_CUDA(cudaSetDevice(ctx->device));
   double* base = nullptr;
-  GS_TRY(gs::scratch_address(ctx->device, &base));
+  GS_TRY(gs::scratch_address(ctx, &base));
   GS_TRY(gs::mas_apply_launch(ctx, mas, r, z, nrhs, base, base + per));
   if (gs::level0_bf16_on_tensor_cores(ctx, mas, nrhs) || gs::level0_f64tc_usable(ctx, mas, nrhs) ||
       gs::level0_f32_bulk_usable(mas, nrhs)) {
