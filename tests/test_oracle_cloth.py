@@ -2,7 +2,10 @@
 mathematics fixes: finite differences where the Hessian is exact, the PSD
 projection of the exact Hessian where it is clamped, the dihedral-angle
 gradient by central differences, closed-form masses, a brute-force dense
-scatter of the triplets, and the independent input generator."""
+scatter of the triplets, the independent input generator, and the
+invariances every element Hessian has (rigid translations in its null space,
+blocks that rotate with the sheet, a dihedral gradient with no net force or
+torque), also where the clamp or the strain limit is active."""
 
 import numpy as np
 import pytest
@@ -173,3 +176,34 @@ def test_oracle_matches_the_independent_generator():
     R1, C1, B1 = assembly.assemble(s.rows, s.cols, s.blocks)
     assert np.array_equal(R0, R1) and np.array_equal(C0, C1)
     assert np.abs(B0 - B1).max() <= 1e-12 * np.abs(B1).max()
+
+
+@pytest.mark.parametrize("stretch", [0.9, 1.02, 1.3])
+def test_element_hessians_are_frame_indifferent_and_translation_free(stretch):
+    # the energies depend on x only through edge vectors and their lengths and
+    # angles, so (i) every element Hessian annihilates a rigid translation
+    # (sum_b H_ab = 0), (ii) rotating the deformed sheet rotates every block
+    # (H_ab(R x) = R H_ab(x) R^T), and (iii) the dihedral gradient sums to zero
+    # and carries no torque (sum_a g_a = 0, sum_a p_a x g_a = 0); this holds
+    # with the stretch clamp (0.9) and the strain limit (1.3) active as well
+    n = 6
+    X, tris = sheet(n)
+    hg = hinges(tris)
+    rng = np.random.default_rng(7)
+    x = X @ np.array([[stretch, 0.04, 0], [0, 1.0, 0], [0, 0, 1]]).T + rng.normal(0, 0.02 / (n - 1), X.shape)
+    E, lam, t = 1e8, 0.05e6, 1e-3
+    w, A = cloth.rest_data(X, tris)
+    He = lambda v: cloth.pullback(w, cloth.membrane_F_hessian(cloth.deformation(v, tris, w), A * t, lam, E))
+    H0 = He(x)
+    scale = np.abs(H0).max()
+    assert np.abs(H0.sum(axis=2)).max() <= 1e-12 * scale  # (i), every row block a
+    R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    HR = He(x @ R.T + rng.normal(size=3))
+    assert np.abs(HR - np.einsum("xp,tabpq,yq->tabxy", R, H0, R)).max() <= 1e-11 * scale  # (ii)
+    P = x[hg]
+    g = cloth.dihedral_gradient(P)
+    gs = np.abs(g).max()
+    assert np.abs(g.sum(axis=1)).max() <= 1e-12 * gs * np.abs(P).max()  # (iii) force balance
+    assert np.abs(np.cross(P, g).sum(axis=1)).max() <= 1e-11 * gs * np.abs(P).max()  # (iii) torque
+    gR = cloth.dihedral_gradient(P @ R.T)
+    assert np.abs(gR - g @ R.T).max() <= 1e-11 * gs
