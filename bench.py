@@ -1792,9 +1792,11 @@ def reference_arm(args, rank, world):
         its = list(_json.load(open(golden))["iterations"].values())
     n_contacts = max(1, 200_000 * args.grid ** 3 // 64 ** 3)
     Es = [float(e) for e in args.sweep.split(",")]
-    res = run_oracle_sample(args.grid, Es, args.warmup + args.steps, iters=20, procs=args.nrhs, cycle=True)
+    # at least one sample of each of the cycle's three phases, however few steps are asked for
+    res = run_oracle_sample(args.grid, Es, max(args.warmup + args.steps, 3), iters=20, procs=args.nrhs,
+                            cycle=True)
     allv, host = res["samples"], res["host"]
-    vals = allv[args.warmup:] or allv[-1:]
+    vals = allv[args.warmup:args.warmup + args.steps] or allv[-1:]
     mean = lambda key: statistics.mean([v[key] for v in vals if v.get(key) is not None] or
                                       [v[key] for v in allv if v.get(key) is not None])
     t_ga, t_pa, t_it, t_par = mean("t_ga"), mean("t_pa"), mean("t_iter"), mean("t_iter_par")

@@ -1,0 +1,28 @@
+"""The benchmark's reference arm (the oracle timed on the host cores) runs
+without a GPU and prints the contract's JSON line, also when fewer steps are
+asked for than its phase cycle has phases."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("steps,warmup", [(1, 1), (2, 3)])
+def test_reference_arm_prints_one_contract_line(steps, warmup):
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--grid", "8",
+                        "--nrhs", "2", "--steps", str(steps), "--warmup", str(warmup)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == steps
+    assert line["warmup"] == warmup and line["higher_is_better"] is True and line["dtype"] == "f64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] == 2
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
