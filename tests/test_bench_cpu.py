@@ -1,6 +1,8 @@
-"""The benchmark's reference arm (the oracle timed on the host cores) runs
-without a GPU and prints the contract's JSON line, also when fewer steps are
-asked for than its phase cycle has phases."""
+"""Host-side logic of the benchmark, without a GPU: the reference arm (the
+oracle timed on the host cores) prints the contract's JSON line, also when
+fewer steps are asked for than its phase cycle has phases, and only on rank
+0; the clock record summarises nvidia-smi samples (median SM clock, throttle
+reasons)."""
 
 import json
 import os
@@ -34,3 +36,21 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--nrhs", "2", "--steps", "1", "--warmup", "1"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip() == "", (r.stdout[-500:], r.stderr[-500:])
+
+
+def test_clock_summary_of_nvidia_smi_lines():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    lines = [
+        "0, 2070, 2070, 900.12, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1965, 2070, 1390.50, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1200.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n",  # a sample the tool could not read
+        "garbled\n",
+    ]
+    c = bench.ClockSampler.summarise(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    hot = lines[:1] + ["0, 1500, 2070, 1000, 0x48, Not Active, Active, Not Active, Not Active\n"]
+    assert bench.ClockSampler.summarise(hot)["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise(["garbled\n"]) is None
