@@ -54,3 +54,23 @@ def test_clock_summary_of_nvidia_smi_lines():
     hot = lines[:1] + ["0, 1500, 2070, 1000, 0x48, Not Active, Active, Not Active, Not Active\n"]
     assert bench.ClockSampler.summarise(hot)["reasons"] == ["hw_thermal_slowdown"]
     assert bench.ClockSampler.summarise(["garbled\n"]) is None
+
+
+def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Done:  # a sampler process that has already exited
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = _Done(), str(path)
+    assert s.stop() == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 1}
+    assert not path.exists()
+    assert bench.ClockSampler(0).stop() is None  # never started
