@@ -499,7 +499,13 @@ int gs_cloth_create(gs_ctx ctx, int32_t n_vertices, const double* X, int64_t n_t
  * hinge in the pair order of (e_0, e_1, o_1, o_2) with a <= b, each at (min,
  * max) of its two vertices (transposed when the first is the larger), then one
  * mass block per vertex; rows, cols device int32 (each may be NULL), blocks
- * device double[9 each] (row-major); gs_cloth_info gives the count. */
+ * device double[9 each] (row-major); gs_cloth_info gives the count.
+ * Asynchronous on the context's stream: the call returns once the kernels are
+ * queued.  Errors: GS_ERR_INVALID (a null argument, a cloth of another
+ * context).  The values are not checked: a deformed triangle with a
+ * zero-length edge direction, or a hinge whose triangle collapsed, gives
+ * non-finite blocks, which gs_build_mas reports as GS_ERR_NOT_SPD and
+ * gs_pcg_solve as GS_ERR_NONFINITE. */
 int gs_cloth_triplets(gs_ctx ctx, gs_cloth c, const double* x, int32_t* rows, int32_t* cols, double* blocks);
 int gs_cloth_info(gs_cloth c, int64_t* n_triplets);
 int gs_cloth_destroy(gs_cloth c);
