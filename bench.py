@@ -775,12 +775,15 @@ def cloth_element_line(args, B, dev, stream, clk):
     sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     inst_peak = props.multi_processor_count * FP64_FMA_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e9  # G instr/s
     inst = CLOTH_FP64_INST_TRI * T + CLOTH_FP64_INST_HINGE * H
+    tm, tb = (recorded_traffic(k, f"cloth{n}") for k in ("k_cloth_membrane", "k_cloth_bending"))
+    traffic = tm + tb if tm is not None and tb is not None else None
     flops = CLOTH_FLOP_TRI * T + CLOTH_FLOP_HINGE * H
     nbytes = T * (3 * 24 + 48 + 8 + 12 + 6 * 80) + H * (4 * 24 + 16 + 8 + 10 * 80) + V * (8 + 80)
     out = {"workload": f"cloth {n}x{n}: {T} triangles, {H} hinges, {V} vertices -> {nt} triplets",
            "value": (T + H) / sec, "unit": "elements/s (triangles + hinges)", "ms_per_launch_sequence": sec * 1e3,
            "roofline": {"bound": "alu", "achieved": inst / sec / 1e9, "peak": inst_peak,
-                        "unit": "G FP64 instr/s", "frac": inst / sec / 1e9 / inst_peak, "traffic": None,
+                        "unit": "G FP64 instr/s", "frac": inst / sec / 1e9 / inst_peak, "traffic": traffic,
+                        "traffic_kernels": "k_cloth_membrane + k_cloth_bending (the mass-block kernel not captured)",
                         "fp64_instr_per_launch": inst, "source_flops_per_launch": flops,
                         "source_tflops": flops / sec / 1e12, "bytes_per_launch": nbytes,
                         "hbm_gbs": nbytes / sec / 1e9,

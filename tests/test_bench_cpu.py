@@ -74,3 +74,24 @@ def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
     assert s.stop() == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 1}
     assert not path.exists()
     assert bench.ClockSampler(0).stop() is None  # never started
+
+
+def test_recorded_traffic_holds_only_while_the_source_is_unchanged(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import hashlib
+
+    import bench
+
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.md").write_text(
+        "| kernel | workload | source | sha256[:16] | DRAM bytes per launch |\n|---|---|---|---|---:|\n"
+        f"| k | w1 | k.cu | {h} | 1234 |\n| k | w2 | k.cu | 0000000000000000 | 99 |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("k", "w1") == 1234.0
+    assert bench.recorded_traffic("k", "w2") is None  # recorded for another version of the source
+    assert bench.recorded_traffic("k", "w3") is None  # never captured
+    src.write_text("__global__ void k() { }\n")  # the kernel changed since the capture
+    assert bench.recorded_traffic("k", "w1") is None
